@@ -1,0 +1,352 @@
+/*
+ * FP64 CPU oracle for PALMAD discord discovery (Zymbler & Kraeva,
+ * "High-performance Time Series Anomaly Discovery on Graphics Processor").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this library.  It shares no code, header
+ * or constant with the CUDA library: it reads the same float32 series and
+ * nothing else.
+ *
+ * Everything is double precision and deliberately plain:
+ *   - window mean / standard deviation:  Eq. 4, evaluated two-pass
+ *     (mu = sum/m, sigma^2 = sum (x-mu)^2 / m, algebraically Eq. 4's
+ *     (1/m) sum x^2 - mu^2, chosen for FP64 accuracy);
+ *   - distance: Eq. 5 applied to the z-normalised windows of Eq. 4
+ *     (NOT the dot-product form of Eq. 6, which the GPU uses);
+ *   - non-self match |i - j| >= m (Sec. 2.1), range discord
+ *     min Dist >= r (Sec. 2.1);
+ *   - brute-force non-self-match nearest neighbour ("matrix profile");
+ *   - DRAG, Algorithm 2: phase 1 candidate selection, phase 2 refinement
+ *     with the early-abandoning distance of Sec. 2.2;
+ *   - MERLIN, Algorithm 1: the r schedule over lengths minL..maxL;
+ *   - greedy top-K and the discord heatmap of Eq. 10.
+ *
+ * Readings of the paper taken here (the paper is garbled or silent):
+ *   R1  r is in distance units; every comparison is d < r on the plain
+ *       (not squared) z-normalised Euclidean distance.
+ *   R2  A window whose sigma <= 2^-22 |mu| is flat.  Two flat windows are at
+ *       distance 0; a flat and a non-flat window are at distance sqrt(2m)
+ *       (correlation taken as 0 in Eq. 6).
+ *   R3  A window with no non-self match (possible when n - m + 1 < 2m) has
+ *       no nearest neighbour and is never a discord.
+ *   R4  DRAG returns the candidates that survive phase 2 (the candidate set
+ *       C), each with its exact nearest-neighbour distance; Algorithm 2's
+ *       "D <- D u c" in the else-branch is read as keeping c in C.
+ *   R5  Top-K per length: the range discords sorted by (nnDist desc, index
+ *       asc), taken greedily; with `exclusive` set, a pick must be at least
+ *       m away from every earlier pick.
+ *   R6  A DRAG call "succeeds" when R5 yields K picks; nnDist_m (the value
+ *       fed to the schedule) is the distance of the K-th pick.
+ *   R7  Algorithm 1 lines 7-11: r = 0.99 nnDist_{m-1} once, then r <- 0.99 r
+ *       on each failure.  Lines 13-17: r = mu - 2 sd of the last five
+ *       nnDist (sample deviation, n-1), then r <- r - sd on each failure
+ *       (the duplicate call with an unchanged r is not repeated).  If sd is
+ *       0 the step is 0.01 mu.
+ *   R8  Loop guards (not in the paper): after 60 halvings, 3000 shrinks of
+ *       1%, or any r <= 0, the call is made with r = 0, where every window
+ *       with a non-self match qualifies; fewer than K picks are then
+ *       returned as they are.
+ *   R9  Heatmap (Eq. 10): row m, column i holds nnDist^2 / (2m) for the
+ *       range discords at the final r of that length and 0 elsewhere; the
+ *       row width is n - minL + 1.
+ *
+ * Parallelism: the brute-force nearest neighbour runs its rows in parallel
+ * and DRAG phase 2 runs its candidates in parallel (each candidate sees the
+ * paper's sequence of s, so the result equals the serial loop's).  Phase 1
+ * is serial, as in Algorithm 2.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_FLAT_REL 2.384185791015625e-07 /* 2^-22 */
+
+/* ---------- window statistics (Eq. 4) ---------- */
+
+static void window_stats(const float *T, int64_t i, int32_t m, double *mu, double *sd) {
+    double s = 0.0;
+    for (int32_t k = 0; k < m; ++k) s += (double)T[i + k];
+    double mean = s / (double)m;
+    double v = 0.0;
+    for (int32_t k = 0; k < m; ++k) {
+        double d = (double)T[i + k] - mean;
+        v += d * d;
+    }
+    *mu = mean;
+    *sd = sqrt(v / (double)m);
+}
+
+static int is_flat(double mu, double sd) { return sd <= ORACLE_FLAT_REL * fabs(mu); }
+
+int oracle_stats(const float *T, int64_t n, int32_t m, double *mu, double *sd) {
+    if (!T || !mu || !sd || m < 1 || n < m) return -1;
+    int64_t N = n - m + 1;
+    for (int64_t i = 0; i < N; ++i) window_stats(T, i, m, &mu[i], &sd[i]);
+    return 0;
+}
+
+/* ---------- distance (Eq. 5 on the z-normalised windows of Eq. 4) ---------- */
+
+/* Squared z-normalised Euclidean distance, summation abandoned (and the
+ * partial sum returned) once it reaches `bound2`. */
+static double zdist2(const float *T, int32_t m, int64_t i, int64_t j, double mui, double sdi,
+                     double muj, double sdj, double bound2) {
+    int fi = is_flat(mui, sdi), fj = is_flat(muj, sdj);
+    if (fi && fj) return 0.0;
+    if (fi || fj) return 2.0 * (double)m;
+    double s = 0.0;
+    for (int32_t k = 0; k < m; ++k) {
+        double a = ((double)T[i + k] - mui) / sdi;
+        double b = ((double)T[j + k] - muj) / sdj;
+        double d = a - b;
+        s += d * d;
+        if (s >= bound2) break;
+    }
+    return s;
+}
+
+double oracle_dist(const float *T, int64_t n, int32_t m, int64_t i, int64_t j) {
+    if (!T || m < 1 || i < 0 || j < 0 || i + m > n || j + m > n) return NAN;
+    double mui, sdi, muj, sdj;
+    window_stats(T, i, m, &mui, &sdi);
+    window_stats(T, j, m, &muj, &sdj);
+    return sqrt(zdist2(T, m, i, j, mui, sdi, muj, sdj, INFINITY));
+}
+
+/* ---------- brute-force nearest non-self match ---------- */
+
+int oracle_mp(const float *T, int64_t n, int32_t m, double *mp, int64_t *mpidx) {
+    if (!T || !mp || m < 1 || n < m) return -1;
+    int64_t N = n - m + 1;
+    double *mu = (double *)malloc(sizeof(double) * N), *sd = (double *)malloc(sizeof(double) * N);
+    if (!mu || !sd) { free(mu); free(sd); return -2; }
+    oracle_stats(T, n, m, mu, sd);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < N; ++i) {
+        double best = INFINITY;
+        int64_t arg = -1;
+        for (int64_t j = 0; j < N; ++j) {
+            if (llabs(i - j) < m) continue;
+            double d2 = zdist2(T, m, i, j, mu[i], sd[i], mu[j], sd[j], INFINITY);
+            if (d2 < best) { best = d2; arg = j; }
+        }
+        mp[i] = sqrt(best);
+        if (mpidx) mpidx[i] = arg;
+    }
+    free(mu);
+    free(sd);
+    return 0;
+}
+
+/* ---------- DRAG (Algorithm 2) ---------- */
+
+/* Range discords of length m at threshold r: writes up to `cap` (index,
+ * nnDist) pairs in ascending index order; *count receives the full number.
+ * Returns 0, or a negative value on bad arguments / allocation failure. */
+int oracle_drag(const float *T, int64_t n, int32_t m, double r, int64_t *out_idx, double *out_nn,
+                int64_t cap, int64_t *count) {
+    if (!T || m < 1 || n < m || !count) return -1;
+    int64_t N = n - m + 1;
+    double *mu = (double *)malloc(sizeof(double) * N), *sd = (double *)malloc(sizeof(double) * N);
+    int64_t *C = (int64_t *)malloc(sizeof(int64_t) * N);
+    if (!mu || !sd || !C) { free(mu); free(sd); free(C); return -2; }
+    oracle_stats(T, n, m, mu, sd);
+    const int prune = r > 0.0; /* d < r never holds for r <= 0 */
+
+    /* Phase 1: select candidates. */
+    int64_t nc = 0;
+    C[nc++] = 0;
+    for (int64_t s = 1; s < N; ++s) {
+        int is_cand = 1;
+        int64_t w = 0;
+        for (int64_t q = 0; q < nc; ++q) {
+            int64_t c = C[q];
+            int keep = 1;
+            if (prune && llabs(s - c) >= m) {
+                double d2 = zdist2(T, m, s, c, mu[s], sd[s], mu[c], sd[c], INFINITY);
+                if (sqrt(d2) < r) { keep = 0; is_cand = 0; }
+            }
+            if (keep) C[w++] = c;
+        }
+        nc = w;
+        if (is_cand) C[nc++] = s;
+    }
+
+    /* Phase 2: refine with the early-abandoning distance. */
+    double *nn2 = (double *)malloc(sizeof(double) * (nc > 0 ? nc : 1));
+    char *alive = (char *)malloc(nc > 0 ? nc : 1);
+    if (!nn2 || !alive) { free(mu); free(sd); free(C); free(nn2); free(alive); return -2; }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nc; ++q) {
+        int64_t c = C[q];
+        double best = INFINITY;
+        char ok = 1;
+        for (int64_t s = 0; s < N && ok; ++s) {
+            if (s == c || llabs(s - c) < m) continue;
+            double d2 = zdist2(T, m, s, c, mu[s], sd[s], mu[c], sd[c], best);
+            if (prune && sqrt(d2) < r) ok = 0;
+            else if (d2 < best) best = d2;
+        }
+        alive[q] = ok && isfinite(best);
+        nn2[q] = best;
+    }
+    int64_t k = 0;
+    for (int64_t q = 0; q < nc; ++q) {
+        if (!alive[q]) continue;
+        if (k < cap) {
+            if (out_idx) out_idx[k] = C[q];
+            if (out_nn) out_nn[k] = sqrt(nn2[q]);
+        }
+        ++k;
+    }
+    *count = k;
+    free(mu); free(sd); free(C); free(nn2); free(alive);
+    return 0;
+}
+
+/* ---------- greedy top-K (reading R5) ---------- */
+
+typedef struct { int64_t idx; double nn; } pick_t;
+
+static int cmp_pick(const void *a, const void *b) {
+    const pick_t *x = (const pick_t *)a, *y = (const pick_t *)b;
+    if (x->nn > y->nn) return -1;
+    if (x->nn < y->nn) return 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+int oracle_topk(const int64_t *idx, const double *nn, int64_t count, int32_t m, int32_t K, int exclusive,
+                int64_t *out_idx, double *out_nn) {
+    if (K < 1 || count < 0) return -1;
+    pick_t *p = (pick_t *)malloc(sizeof(pick_t) * (count > 0 ? count : 1));
+    if (!p) return -2;
+    for (int64_t q = 0; q < count; ++q) { p[q].idx = idx[q]; p[q].nn = nn[q]; }
+    qsort(p, (size_t)count, sizeof(pick_t), cmp_pick);
+    int32_t got = 0;
+    for (int64_t q = 0; q < count && got < K; ++q) {
+        int ok = 1;
+        if (exclusive)
+            for (int32_t g = 0; g < got; ++g)
+                if (llabs(p[q].idx - out_idx[g]) < m) { ok = 0; break; }
+        if (ok) { out_idx[got] = p[q].idx; out_nn[got] = p[q].nn; ++got; }
+    }
+    for (int32_t g = got; g < K; ++g) { out_idx[g] = -1; out_nn[g] = 0.0; }
+    free(p);
+    return got;
+}
+
+/* ---------- MERLIN (Algorithm 1) ---------- */
+
+typedef struct {
+    int64_t *idx; double *nn; int64_t cap; int64_t count;
+} drag_buf;
+
+static int run_drag(const float *T, int64_t n, int32_t m, double r, drag_buf *b) {
+    for (;;) {
+        int64_t cnt = 0;
+        int rc = oracle_drag(T, n, m, r, b->idx, b->nn, b->cap, &cnt);
+        if (rc) return rc;
+        if (cnt <= b->cap) { b->count = cnt; return 0; }
+        free(b->idx); free(b->nn);
+        b->cap = cnt;
+        b->idx = (int64_t *)malloc(sizeof(int64_t) * cnt);
+        b->nn = (double *)malloc(sizeof(double) * cnt);
+        if (!b->idx || !b->nn) return -2;
+    }
+}
+
+/* One DRAG call of the schedule: returns 1 on success (K picks), 0 otherwise. */
+static int drag_and_pick(const float *T, int64_t n, int32_t m, double r, int32_t K, int exclusive,
+                         drag_buf *b, int64_t *pidx, double *pnn, int *rc) {
+    *rc = run_drag(T, n, m, r, b);
+    if (*rc) return 0;
+    int got = oracle_topk(b->idx, b->nn, b->count, m, K, exclusive, pidx, pnn);
+    if (got < 0) { *rc = got; return 0; }
+    return got == K;
+}
+
+/*
+ * out_idx/out_nn: [L*K] picks per length (index -1 and 0.0 when fewer);
+ * out_count: [L] number of range discords at the final r; out_r: [L] final r;
+ * out_calls: [L] DRAG calls made; out_heat: [L*(n-minL+1)] or NULL.
+ */
+int oracle_merlin(const float *T, int64_t n, int32_t minL, int32_t maxL, int32_t K, int exclusive,
+                  int64_t *out_idx, double *out_nn, int64_t *out_count, double *out_r,
+                  int32_t *out_calls, float *out_heat) {
+    if (!T || minL < 3 || maxL < minL || n < 2 * (int64_t)maxL || K < 1) return -1;
+    const int32_t L = maxL - minL + 1;
+    const int64_t W = n - minL + 1;
+    drag_buf b = {0};
+    b.cap = 1024;
+    b.idx = (int64_t *)malloc(sizeof(int64_t) * b.cap);
+    b.nn = (double *)malloc(sizeof(double) * b.cap);
+    double *sched = (double *)malloc(sizeof(double) * L); /* nnDist_m fed to the schedule */
+    if (!b.idx || !b.nn || !sched) { free(b.idx); free(b.nn); free(sched); return -2; }
+    if (out_heat) memset(out_heat, 0, sizeof(float) * (size_t)L * (size_t)W);
+    int rc = 0;
+    for (int32_t m = minL; m <= maxL && !rc; ++m) {
+        const int32_t l = m - minL;
+        int64_t *pidx = out_idx + (int64_t)l * K;
+        double *pnn = out_nn + (int64_t)l * K;
+        int calls = 0, ok = 0;
+        double r;
+        if (l == 0) {
+            r = 2.0 * sqrt((double)minL);
+            for (int h = 0;; ++h) {
+                if (h >= 60) r = 0.0;
+                ok = drag_and_pick(T, n, m, r, K, exclusive, &b, pidx, pnn, &rc); ++calls;
+                if (ok || rc || r <= 0.0) break;
+                r = 0.5 * r;
+            }
+        } else if (l <= 4) {
+            r = 0.99 * sched[l - 1];
+            for (int h = 0;; ++h) {
+                if (h >= 3000 || r <= 0.0) r = 0.0;
+                ok = drag_and_pick(T, n, m, r, K, exclusive, &b, pidx, pnn, &rc); ++calls;
+                if (ok || rc || r <= 0.0) break;
+                r = 0.99 * r;
+            }
+        } else {
+            double mean = 0.0, var = 0.0;
+            for (int q = 1; q <= 5; ++q) mean += sched[l - q];
+            mean /= 5.0;
+            for (int q = 1; q <= 5; ++q) var += (sched[l - q] - mean) * (sched[l - q] - mean);
+            double sdv = sqrt(var / 4.0);
+            double step = sdv > 0.0 ? sdv : 0.01 * mean;
+            r = mean - 2.0 * sdv;
+            for (int h = 0;; ++h) {
+                if (h >= 3000 || r <= 0.0) r = 0.0;
+                ok = drag_and_pick(T, n, m, r, K, exclusive, &b, pidx, pnn, &rc); ++calls;
+                if (ok || rc || r <= 0.0) break;
+                r = step > 0.0 ? r - step : 0.0;
+            }
+        }
+        if (rc) break;
+        /* nnDist_m: distance of the K-th pick (or of the last pick when fewer). */
+        int got = 0;
+        while (got < K && pidx[got] >= 0) ++got;
+        sched[l] = got > 0 ? pnn[got - 1] : 0.0;
+        if (out_count) out_count[l] = b.count;
+        if (out_r) out_r[l] = r;
+        if (out_calls) out_calls[l] = calls;
+        if (out_heat) {
+            float *row = out_heat + (int64_t)l * W;
+            for (int64_t q = 0; q < b.count; ++q)
+                row[b.idx[q]] = (float)(b.nn[q] * b.nn[q] / (2.0 * (double)m));
+        }
+    }
+    free(b.idx); free(b.nn); free(sched);
+    return rc;
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
