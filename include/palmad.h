@@ -1,0 +1,206 @@
+/*
+ * palmad.h -- C ABI of the GB300-native PALMAD discord engine (libpalmad.so).
+ *
+ * PALMAD (Zymbler & Kraeva, "High-performance Time Series Anomaly Discovery
+ * on Graphics Processor") finds, for every subsequence length m in
+ * [minL, maxL], the range discords of a time series: the length-m windows
+ * whose z-normalised Euclidean distance to their nearest non-self match
+ * (|i - j| >= m) is at least r (Sec. 2.1).  Each length runs the two DRAG
+ * phases (candidate selection, then refinement to the exact nearest-neighbour
+ * distance; Algorithm 2, parallelised as Algorithms 3-4) under the MERLIN
+ * threshold schedule (Algorithm 1), with the window statistics carried from
+ * m to m+1 by Eq. 7-8.
+ *
+ * Conventions used by every entry point:
+ *   - Indices are 0-based (paper index i+1 <-> index i here).
+ *   - Distances are plain z-normalised Euclidean distances ED_norm (not
+ *     squared); r is in the same unit.  A window is a range discord when its
+ *     nearest-neighbour distance d satisfies d >= r (Sec. 2.1); pruning uses
+ *     the strict d < r of Algorithm 2.
+ *   - A window with sigma <= 2^-22 |mu| is flat: two flat windows are at
+ *     distance 0, a flat and a non-flat window at sqrt(2m).  A window with
+ *     no non-self match (possible only when n - m + 1 < 2m) is never a
+ *     discord.
+ *   - Per length, the top-K are the range discords at that length's final r
+ *     sorted by (distance desc, index asc) and taken greedily; with
+ *     exclusive_topk set, each pick lies at least m away from earlier picks.
+ *     MERLIN's schedule reads the distance of the K-th pick.  A length whose
+ *     schedule reached r = 0 without K picks reports fewer (index -1,
+ *     distance 0).
+ *   - The schedule (Algorithm 1): r = 2 sqrt(minL), halved until K picks;
+ *     for the next four lengths r = 0.99 d_{m-1}, times 0.99 on failure;
+ *     afterwards r = mean - 2 sd of the previous five d (sample deviation),
+ *     minus sd on failure (0.01 mean when sd = 0).  After 60 halvings, 3000
+ *     shrink steps or r <= 0 the call uses r = 0.
+ *   - Results are exact: discord indices equal those of an FP64 evaluation
+ *     and distances are recomputed in FP64.
+ *
+ * Ownership: every pointer argument belongs to the caller and is only read
+ * or written during the call.  The context owns all device memory it
+ * allocates (grown on demand, freed by palmad_destroy) and one CUDA stream
+ * (or borrows the caller's).  A context must not be used by two threads at
+ * once.
+ *
+ * Errors: every entry point returns a palmad_status.  On a negative status
+ * no output array has been written, and palmad_last_error() describes the
+ * failure.
+ */
+#ifndef PALMAD_H
+#define PALMAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct palmad_ctx palmad_ctx;
+
+typedef enum {
+    PALMAD_OK = 0,
+    PALMAD_ERR_ARG = -1,         /* an argument violates the rules above */
+    PALMAD_ERR_NONFINITE = -2,   /* T holds a NaN or an infinity */
+    PALMAD_ERR_OOM = -3,         /* device or pinned host allocation failed */
+    PALMAD_ERR_CUDA = -4,        /* a CUDA runtime call or kernel failed */
+    PALMAD_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    PALMAD_ERR_UNSUPPORTED = -6, /* option or size not supported by this build */
+    PALMAD_ERR_INTERNAL = -7     /* an internal consistency check failed */
+} palmad_status;
+
+/* Arithmetic of the pair evaluations (the candidate-select and refine dot
+ * products).  Every form re-checks undecided pairs and recomputes the final
+ * nearest-neighbour distances in FP64, so all forms return identical
+ * results. */
+typedef enum {
+    PALMAD_PREC_FP32 = 0,   /* CUDA-core FP32 (plain form) */
+    PALMAD_PREC_MIXED = 1   /* tensor-core refine where supported, else FP32 */
+} palmad_precision;
+
+typedef struct {
+    int32_t struct_size;     /* sizeof(palmad_options); set by palmad_default_options */
+    int32_t precision;       /* palmad_precision */
+    int32_t exclusive_topk;  /* 1 (default): top-K picks mutually >= m apart; 0: plain top-K */
+    int32_t batch_lengths;   /* 0/1: one DRAG call per schedule step (plain form);
+                                W > 1: lengths run W at a time with a speculative r
+                                and an exact host replay of the schedule (batched form) */
+    double band_rel;         /* pairs with |d - r| < band_rel * r are re-checked in FP64
+                                (floor; the build's FP32 error bound is applied on top);
+                                default 1e-3, must lie in [1e-6, 0.1] */
+    int32_t select_cap;      /* max columns a select strip scans past its first
+                                (0 = default); pairs left unscanned go to refine */
+    int32_t use_graph;       /* 1: capture the batched form's launches in a CUDA graph */
+    int32_t profile;         /* 1: time every kernel launch with CUDA events
+                                (palmad_get_stats) */
+    int32_t reserved[5];
+} palmad_options;
+
+/* Per-call counters of the most recent find/drag call. */
+typedef struct {
+    int32_t struct_size;        /* sizeof(palmad_stats) */
+    int32_t lengths;            /* lengths processed */
+    int64_t drag_calls;         /* DRAG evaluations the schedule asked for */
+    int64_t device_passes;      /* select+refine passes actually launched */
+    int64_t reruns;             /* batched form: lengths rerun with a lower r */
+    int64_t select_pairs;       /* pairs evaluated by candidate select */
+    int64_t refine_pairs;       /* pairs evaluated by refine (FP32 or tensor) */
+    int64_t fp64_pairs;         /* pairs re-evaluated in FP64 */
+    int64_t survivors;          /* candidates handed from select to refine (sum) */
+    int64_t discords;           /* range discords at the final r (sum over lengths) */
+    double max_fp32_rho_err;    /* max |rho_fast - rho_fp64| seen on re-checked pairs */
+    /* profile == 1: per-kernel totals (index = palmad_kernel_id) */
+    int64_t launches[8];
+    double kernel_ms[8];
+} palmad_stats;
+
+/* Kernel ids for palmad_stats.launches / kernel_ms. */
+enum {
+    PALMAD_K_STATS = 0,   /* window statistics init / Eq. 7-8 advance */
+    PALMAD_K_SELECT = 1,  /* candidate select (Algorithm 3) */
+    PALMAD_K_COMPACT = 2, /* bitmap -> survivor list (Algorithm 4 line 2) */
+    PALMAD_K_REFINE = 3,  /* refine, fast pass (Algorithm 4) */
+    PALMAD_K_RECHECK = 4, /* refine, FP64 re-check of the near-minimum pairs */
+    PALMAD_K_TOPK = 5,    /* discord gather + per-length top-K */
+    PALMAD_K_HEAT = 6,    /* heatmap row write (Eq. 10) */
+    PALMAD_K_OTHER = 7
+};
+
+/* Fills *opt with the defaults (FP32, exclusive top-K, plain form,
+ * band_rel 1e-3).  Returns PALMAD_ERR_ARG when opt is NULL. */
+palmad_status palmad_default_options(palmad_options *opt);
+
+/* Creates a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t to borrow (the context then never destroys it) or NULL to
+ * create a private non-blocking stream.  *out is NULL on failure. */
+palmad_status palmad_create(palmad_ctx **out, int device, void *cuda_stream);
+
+/* Frees every resource of the context (NULL is a no-op). */
+void palmad_destroy(palmad_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none); valid until the
+ * next call on the context. */
+const char *palmad_last_error(const palmad_ctx *ctx);
+
+/*
+ * MERLIN over one series (Algorithm 1; DRAG per schedule step, Algorithms
+ * 2-4).  Host pointers.
+ *   T           [n] float32 series, finite.
+ *   n           series length; must satisfy n >= 2 * maxL.
+ *   minL, maxL  3 <= minL <= maxL (Eq. 2: 3 <= m).
+ *   topK        1 <= topK <= 1024.
+ *   opt         NULL for the defaults.
+ *   out_idx     [L * topK] int64, L = maxL - minL + 1, row-major by length;
+ *               discord start indices, -1 where fewer than topK were found.
+ *   out_nndist  [L * topK] double, their nearest-neighbour distances
+ *               (ED_norm, FP64), 0.0 where the index is -1.
+ *   out_count   [L] or NULL: number of range discords at each final r.
+ *   out_r       [L] or NULL: the final r of each length.
+ *   out_heatmap [L * (n - minL + 1)] float32 or NULL: row l = length
+ *               minL + l holds nnDist^2 / (2m) at every range discord of
+ *               that length and 0 elsewhere (Eq. 10).
+ */
+palmad_status palmad_find_discords(palmad_ctx *ctx, const float *T, int64_t n, int32_t minL, int32_t maxL,
+                                   int32_t topK, const palmad_options *opt, int64_t *out_idx,
+                                   double *out_nndist, int64_t *out_count, double *out_r, float *out_heatmap);
+
+/* As palmad_find_discords, but T and every output are DEVICE pointers on
+ * the context's device; the call is stream-ordered on the context's stream
+ * and returns after the results are written. */
+palmad_status palmad_find_discords_device(palmad_ctx *ctx, const float *T_dev, int64_t n, int32_t minL,
+                                          int32_t maxL, int32_t topK, const palmad_options *opt,
+                                          int64_t *out_idx_dev, double *out_nndist_dev,
+                                          int64_t *out_count_dev, double *out_r_dev, float *out_heatmap_dev);
+
+/*
+ * MERLIN over `count` independent series (the batched form's multi-series
+ * entry).  Host pointers; series s has T[s][0..n[s]), lengths
+ * minL[s]..maxL[s] and writes out_idx[s] / out_nndist[s]
+ * ([L_s * topK] each) and, when the arrays are non-NULL, out_count[s] and
+ * out_r[s] ([L_s] each).  Same rules per series as palmad_find_discords.
+ */
+palmad_status palmad_find_discords_batch(palmad_ctx *ctx, int32_t count, const float *const *T, const int64_t *n,
+                                         const int32_t *minL, const int32_t *maxL, int32_t topK,
+                                         const palmad_options *opt, int64_t *const *out_idx,
+                                         double *const *out_nndist, int64_t *const *out_count,
+                                         double *const *out_r);
+
+/*
+ * One DRAG call (Algorithm 2; Algorithms 3-4): every range discord of
+ * length m at threshold r, in ascending index order.  Host pointers.
+ *   T [n] float32, finite; 3 <= m; n >= 2m.
+ *   out_idx / out_nndist: [cap] arrays receiving the first min(cap, count)
+ *   discords (index, FP64 distance); *out_count receives the full count.
+ */
+palmad_status palmad_drag(palmad_ctx *ctx, const float *T, int64_t n, int32_t m, double r, const palmad_options *opt,
+                          int64_t *out_idx, double *out_nndist, int64_t cap, int64_t *out_count);
+
+/* Counters of the most recent find/drag call on this context. */
+palmad_status palmad_get_stats(const palmad_ctx *ctx, palmad_stats *out);
+
+/* Library version string. */
+const char *palmad_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PALMAD_H */

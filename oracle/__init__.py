@@ -52,6 +52,7 @@ def _load():
             lib.oracle_dist.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64]
             lib.oracle_dist.restype = ctypes.c_double
             lib.oracle_mp.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, _f64p, _i64p]
+            lib.oracle_nn_one.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _f64p, _i64p]
             lib.oracle_drag.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _i64p, _f64p,
                                         ctypes.c_int64, _i64p]
             lib.oracle_topk.argtypes = [_i64p, _f64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
@@ -101,6 +102,16 @@ def matrix_profile(T, m: int):
     if rc:
         raise ValueError(f"oracle_mp rc={rc}")
     return mp, idx
+
+
+def nn_one(T, m: int, i: int):
+    """Brute-force nearest non-self match of window i: (distance, index)."""
+    T = _f32(T)
+    nn, idx = ctypes.c_double(0.0), ctypes.c_int64(0)
+    rc = _load().oracle_nn_one(_p(T, _f32p), len(T), m, i, ctypes.byref(nn), ctypes.byref(idx))
+    if rc:
+        raise ValueError(f"oracle_nn_one rc={rc}")
+    return nn.value, idx.value
 
 
 def drag(T, m: int, r: float):

@@ -142,6 +142,36 @@ int oracle_mp(const float *T, int64_t n, int32_t m, double *mp, int64_t *mpidx) 
     return 0;
 }
 
+/* Nearest non-self match of one window (one row of the brute force above). */
+int oracle_nn_one(const float *T, int64_t n, int32_t m, int64_t i, double *nn, int64_t *nnidx) {
+    if (!T || !nn || m < 1 || n < m || i < 0 || i > n - m) return -1;
+    int64_t N = n - m + 1;
+    double mui, sdi;
+    window_stats(T, i, m, &mui, &sdi);
+    double best = INFINITY;
+    int64_t arg = -1;
+#pragma omp parallel
+    {
+        double lb = INFINITY;
+        int64_t la = -1;
+#pragma omp for schedule(static)
+        for (int64_t j = 0; j < N; ++j) {
+            if (llabs(i - j) < m) continue;
+            double muj, sdj;
+            window_stats(T, j, m, &muj, &sdj);
+            double d2 = zdist2(T, m, i, j, mui, sdi, muj, sdj, INFINITY);
+            if (d2 < lb || (d2 == lb && j < la)) { lb = d2; la = j; }
+        }
+#pragma omp critical
+        {
+            if (lb < best || (lb == best && la >= 0 && la < arg)) { best = lb; arg = la; }
+        }
+    }
+    *nn = sqrt(best);
+    if (nnidx) *nnidx = arg;
+    return 0;
+}
+
 /* ---------- DRAG (Algorithm 2) ---------- */
 
 /* Range discords of length m at threshold r: writes up to `cap` (index,

@@ -1,0 +1,134 @@
+// Window statistics: mean and deviation of every length-m window (Eq. 4),
+// carried from m to m+1 by the recurrences of Eq. 7-8 (Sec. 3.1.1), plus the
+// per-window FP32 records the pair kernels read and the candidate bitmap.
+#include "palmad_dev.cuh"
+
+namespace palmad {
+
+namespace {
+
+constexpr int kRun = 16;                              // windows per thread in the init pass
+constexpr double kFlatRel = 2.384185791015625e-07;    // 2^-22: flat window threshold
+constexpr double kNearFlatRel = 3.814697265625e-06;   // 2^-18: recompute two-pass below this
+
+// Initial statistics at the first length (Eq. 4).  Each thread slides over
+// kRun consecutive windows with sums shifted by the run's first value; a
+// window whose deviation comes out near the flat threshold is recomputed
+// two-pass so that the flat decision is exact.
+__global__ void k_stats_init(const float* __restrict__ T, int64_t n, int32_t m, double* __restrict__ mu,
+                             double* __restrict__ var, int32_t* __restrict__ flags) {
+    const int64_t N = n - m + 1;
+    const int64_t i0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kRun;
+    if (i0 >= N) return;
+    const double tref = T[i0];
+    double S = 0.0, SS = 0.0;
+    bool bad = false;
+    for (int k = 0; k < m; ++k) {
+        const float x = T[i0 + k];
+        bad |= !isfinite(x);
+        const double d = double(x) - tref;
+        S += d;
+        SS += d * d;
+    }
+    const double inv_m = 1.0 / double(m);
+    const int64_t i1 = min(i0 + kRun, N);
+    for (int64_t i = i0; i < i1; ++i) {
+        if (i > i0) {
+            const float xa = T[i + m - 1], xr = T[i - 1];
+            bad |= !isfinite(xa);
+            const double da = double(xa) - tref, dr = double(xr) - tref;
+            S += da - dr;
+            SS += da * da - dr * dr;
+        }
+        const double mean_s = S * inv_m;
+        double v = fmax(SS * inv_m - mean_s * mean_s, 0.0);
+        double mean = tref + mean_s;
+        if (v <= (kNearFlatRel * mean) * (kNearFlatRel * mean)) {
+            double s2 = 0.0;
+            for (int k = 0; k < m; ++k) s2 += double(T[i + k]);
+            mean = s2 * inv_m;
+            double q = 0.0;
+            for (int k = 0; k < m; ++k) {
+                const double d = double(T[i + k]) - mean;
+                q += d * d;
+            }
+            v = q * inv_m;
+        }
+        mu[i] = mean;
+        var[i] = v;
+    }
+    if (bad) atomicOr(flags, 1);
+}
+
+// New (mu, var) of window i at length m from its values at m-1 (Eq. 7-8).
+__device__ __forceinline__ void advance_one(double mu_o, double var_o, float t_new, int32_t m, double& mu_n,
+                                            double& var_n) {
+    const double mm1 = double(m - 1), inv_m = 1.0 / double(m);
+    const double d = mu_o - double(t_new);
+    mu_n = (mm1 * mu_o + double(t_new)) * inv_m;
+    var_n = mm1 * inv_m * (var_o + d * d * inv_m);
+}
+
+__global__ void k_stats_step(const StatsArgs a) {
+    const int64_t N = a.n - a.m + 1;
+    const int64_t P = (N + 31) / 32;
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const int32_t m = a.m;
+    bool any_flat = false;
+    for (int64_t i = tid; i < N; i += stride) {
+        double mu_i, var_i;
+        const float t_add = a.T[i + m - 1];
+        if (a.advance) advance_one(a.mu_old[i], a.var_old[i], t_add, m, mu_i, var_i);
+        else { mu_i = a.mu_old[i]; var_i = a.var_old[i]; }
+        a.mu[i] = mu_i;
+        a.var[i] = var_i;
+        const double sd = sqrt(var_i);
+        const bool flat = sd <= kFlatRel * fabs(mu_i);
+        any_flat |= flat;
+        float df = 0.f, dg = 0.f;
+        if (i >= 1) {
+            double mu_p, var_p;
+            const float t_rm = a.T[i - 1];
+            if (a.advance) advance_one(a.mu_old[i - 1], a.var_old[i - 1], a.T[i + m - 2], m, mu_p, var_p);
+            else mu_p = a.mu_old[i - 1];
+            df = float(0.5 * (double(t_add) - double(t_rm)));
+            dg = float((double(t_add) - mu_i) + (double(t_rm) - mu_p));
+        }
+        const float inv = flat ? 0.f : float(1.0 / (sqrt(double(m)) * sd));
+        a.win[i] = make_float4(df, dg, inv, float(mu_i));
+    }
+    // Candidate bitmap: a window starts alive iff it has a non-self match.
+    for (int64_t w = tid; w < P; w += stride) {
+        uint32_t word = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t i = w * 32 + b;
+            if (i < N && (i + m <= N - 1 || i - m >= 0)) word |= 1u << b;
+        }
+        a.bits[w] = word;
+    }
+    if (any_flat) atomicOr(a.flags, 2);
+}
+
+}  // namespace
+
+cudaError_t launch_stats_init(const float* T, int64_t n, int32_t m, double* mu, double* var, int32_t* flags,
+                              cudaStream_t s) {
+    const int64_t N = n - m + 1;
+    const int64_t threads = (N + kRun - 1) / kRun;
+    const int block = 128;
+    const int grid = int((threads + block - 1) / block);
+    k_stats_init<<<grid, block, 0, s>>>(T, n, m, mu, var, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_step(const StatsArgs& a, cudaStream_t s) {
+    const int64_t N = a.n - a.m + 1;
+    const int block = 256;
+    int64_t grid = (N + block - 1) / block;
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_stats_step<<<int(grid), block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace palmad

@@ -1,0 +1,232 @@
+"""Thin ctypes binding of libpalmad.so (include/palmad.h).
+
+Argument marshalling only: every step of discord discovery runs in the CUDA
+library.  Loading fails loudly when the library is missing -- there is no CPU
+fallback.  Host arrays are numpy; the ``*_device`` entry takes torch CUDA
+tensors (torch serves as the device-memory allocator only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpalmad.so")
+
+PALMAD_OK = 0
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NONFINITE", -3: "ERR_OOM", -4: "ERR_CUDA", -5: "ERR_TIMEOUT",
+          -6: "ERR_UNSUPPORTED", -7: "ERR_INTERNAL"}
+PREC_FP32, PREC_MIXED = 0, 1
+KERNELS = ["stats", "select", "compact", "refine", "recheck", "topk", "heat", "other"]
+
+
+class PalmadError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("exclusive_topk", ctypes.c_int32),
+        ("batch_lengths", ctypes.c_int32),
+        ("band_rel", ctypes.c_double),
+        ("select_cap", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+        ("profile", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_int32),
+        ("lengths", ctypes.c_int32),
+        ("drag_calls", ctypes.c_int64),
+        ("device_passes", ctypes.c_int64),
+        ("reruns", ctypes.c_int64),
+        ("select_pairs", ctypes.c_int64),
+        ("refine_pairs", ctypes.c_int64),
+        ("fp64_pairs", ctypes.c_int64),
+        ("survivors", ctypes.c_int64),
+        ("discords", ctypes.c_int64),
+        ("max_fp32_rho_err", ctypes.c_double),
+        ("launches", ctypes.c_int64 * 8),
+        ("kernel_ms", ctypes.c_double * 8),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("launches", "kernel_ms", "struct_size")}
+        d["launches"] = {KERNELS[i]: int(self.launches[i]) for i in range(8)}
+        d["kernel_ms"] = {KERNELS[i]: float(self.kernel_ms[i]) for i in range(8)}
+        return d
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+def load(path: str = LIB_PATH):
+    """Load libpalmad.so (raises if it is missing or does not load)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpalmad.so not found at {path}; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    lib.palmad_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.palmad_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp]
+    lib.palmad_destroy.argtypes = [_vp]
+    lib.palmad_destroy.restype = None
+    lib.palmad_last_error.argtypes = [_vp]
+    lib.palmad_last_error.restype = ctypes.c_char_p
+    lib.palmad_version.restype = ctypes.c_char_p
+    lib.palmad_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
+    lib.palmad_find_discords.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(Options), _vp, _vp, _vp, _vp, _vp]
+    lib.palmad_find_discords_device.argtypes = lib.palmad_find_discords.argtypes
+    lib.palmad_find_discords_batch.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_int32,
+                                               ctypes.POINTER(Options), _vp, _vp, _vp, _vp]
+    lib.palmad_drag.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                ctypes.POINTER(Options), _vp, _vp, ctypes.c_int64, _i64p]
+    for name in ("palmad_default_options", "palmad_create", "palmad_get_stats", "palmad_find_discords",
+                 "palmad_find_discords_device", "palmad_find_discords_batch", "palmad_drag"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def palmad_version() -> str:
+    return load().palmad_version().decode()
+
+
+def palmad_default_options(**kw) -> Options:
+    o = Options()
+    load().palmad_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a) -> int:
+    return a.ctypes.data if a is not None else None
+
+
+class Context:
+    """A palmad_ctx on one CUDA device (palmad_create / palmad_destroy)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self._lib = load()
+        self._h = _vp()
+        st = self._lib.palmad_create(ctypes.byref(self._h), device, stream)
+        if st != PALMAD_OK:
+            raise PalmadError(st, "palmad_create failed")
+
+    def close(self):
+        if self._h:
+            self._lib.palmad_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int):
+        if st != PALMAD_OK:
+            raise PalmadError(st, self._lib.palmad_last_error(self._h).decode())
+
+    def palmad_last_error(self) -> str:
+        return self._lib.palmad_last_error(self._h).decode()
+
+    def palmad_get_stats(self) -> dict:
+        s = Stats()
+        s.struct_size = ctypes.sizeof(Stats)
+        self._check(self._lib.palmad_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def palmad_find_discords(self, T, minL: int, maxL: int, topK: int, options: Options | None = None,
+                             heatmap: bool = False) -> dict:
+        """Host-memory MERLIN over one series; see palmad_find_discords in palmad.h."""
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        L = maxL - minL + 1
+        idx = np.empty((L, topK), dtype=np.int64)
+        nn = np.empty((L, topK), dtype=np.float64)
+        cnt = np.empty(L, dtype=np.int64)
+        rr = np.empty(L, dtype=np.float64)
+        heat = np.empty((L, len(T) - minL + 1), dtype=np.float32) if heatmap else None
+        self._check(self._lib.palmad_find_discords(
+            self._h, _ptr(T), len(T), minL, maxL, topK, ctypes.byref(options) if options else None,
+            _ptr(idx), _ptr(nn), _ptr(cnt), _ptr(rr), _ptr(heat)))
+        out = {"idx": idx, "nn": nn, "count": cnt, "r": rr}
+        if heat is not None:
+            out["heatmap"] = heat
+        return out
+
+    def palmad_find_discords_device(self, T_dev, minL: int, maxL: int, topK: int,
+                                    options: Options | None = None, heatmap_dev=None) -> dict:
+        """Device-memory MERLIN: T_dev is a float32 CUDA tensor; outputs are
+        CUDA tensors on the same device (allocated here through torch)."""
+        import torch
+        assert T_dev.is_cuda and T_dev.dtype == torch.float32 and T_dev.is_contiguous()
+        L = maxL - minL + 1
+        dev = T_dev.device
+        idx = torch.empty((L, topK), dtype=torch.int64, device=dev)
+        nn = torch.empty((L, topK), dtype=torch.float64, device=dev)
+        cnt = torch.empty(L, dtype=torch.int64, device=dev)
+        rr = torch.empty(L, dtype=torch.float64, device=dev)
+        self._check(self._lib.palmad_find_discords_device(
+            self._h, T_dev.data_ptr(), T_dev.numel(), minL, maxL, topK,
+            ctypes.byref(options) if options else None, idx.data_ptr(), nn.data_ptr(), cnt.data_ptr(),
+            rr.data_ptr(), heatmap_dev.data_ptr() if heatmap_dev is not None else None))
+        return {"idx": idx, "nn": nn, "count": cnt, "r": rr}
+
+    def palmad_find_discords_batch(self, series, minL, maxL, topK: int, options: Options | None = None) -> list:
+        """Independent series in one call; returns one result dict per series."""
+        count = len(series)
+        Ts = [np.ascontiguousarray(s, dtype=np.float32) for s in series]
+        ns = np.array([len(s) for s in Ts], dtype=np.int64)
+        mins = np.ascontiguousarray(minL, dtype=np.int32)
+        maxs = np.ascontiguousarray(maxL, dtype=np.int32)
+        outs = []
+        for a, b in zip(mins, maxs):
+            L = int(b) - int(a) + 1
+            outs.append({"idx": np.empty((L, topK), dtype=np.int64), "nn": np.empty((L, topK)),
+                         "count": np.empty(L, dtype=np.int64), "r": np.empty(L)})
+        arr = lambda xs: (ctypes.c_void_p * count)(*[x.ctypes.data for x in xs])  # noqa: E731
+        self._check(self._lib.palmad_find_discords_batch(
+            self._h, count, arr(Ts), _ptr(ns), _ptr(mins), _ptr(maxs), topK,
+            ctypes.byref(options) if options else None,
+            arr([o["idx"] for o in outs]), arr([o["nn"] for o in outs]),
+            arr([o["count"] for o in outs]), arr([o["r"] for o in outs])))
+        return outs
+
+    def palmad_drag(self, T, m: int, r: float, options: Options | None = None):
+        """All range discords of length m at threshold r (ascending index)."""
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        cap = 4096
+        while True:
+            idx = np.empty(cap, dtype=np.int64)
+            nn = np.empty(cap, dtype=np.float64)
+            cnt = ctypes.c_int64(0)
+            self._check(self._lib.palmad_drag(self._h, _ptr(T), len(T), m, float(r),
+                                              ctypes.byref(options) if options else None,
+                                              _ptr(idx), _ptr(nn), cap, ctypes.byref(cnt)))
+            if cnt.value <= cap:
+                return idx[:cnt.value].copy(), nn[:cnt.value].copy()
+            cap = cnt.value

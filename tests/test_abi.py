@@ -1,0 +1,80 @@
+"""CPU-side checks of the C ABI library: it loads and exports every entry
+point include/palmad.h declares; host-side argument and option rules that
+need no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "palmad.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(palmad_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2304_01660_gb300 import _build, palmad
+    _build.build()
+    return palmad.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ["palmad_create", "palmad_destroy", "palmad_find_discords", "palmad_find_discords_device",
+                 "palmad_find_discords_batch", "palmad_drag", "palmad_last_error", "palmad_default_options",
+                 "palmad_get_stats", "palmad_version"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_default_options_and_version(lib):
+    from paper_2304_01660_gb300 import palmad
+    o = palmad.palmad_default_options()
+    assert o.struct_size == ctypes.sizeof(palmad.Options)
+    assert o.exclusive_topk == 1 and o.band_rel == pytest.approx(1e-3)
+    assert lib.palmad_default_options(None) == -1
+    assert "sm_103a" in palmad.palmad_version()
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of palmad_options / palmad_stats match the C layout
+    (a C probe compiled against the header prints sizes and offsets)."""
+    import subprocess
+    from paper_2304_01660_gb300 import palmad
+    probe = tmp_path / "probe.c"
+    probe.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "palmad.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(palmad_options), offsetof(palmad_options, band_rel),
+         offsetof(palmad_options, profile), sizeof(palmad_stats), offsetof(palmad_stats, max_fp32_rho_err),
+         offsetof(palmad_stats, kernel_ms));
+  return 0;
+}
+""")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(probe), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    O, S = palmad.Options, palmad.Stats
+    assert got == [ctypes.sizeof(O), O.band_rel.offset, O.profile.offset, ctypes.sizeof(S),
+                   S.max_fp32_rho_err.offset, S.kernel_ms.offset]
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.palmad_create(ctypes.byref(h), 0, None) != 0
+    assert not h.value

@@ -150,6 +150,16 @@ def test_profile_matches_python_brute_force(n, m, seed):
         assert oracle.dist(T, m, i, idx[i]) == pytest.approx(mp[i], rel=1e-12, abs=1e-12)
 
 
+def test_nn_one_matches_profile_rows():
+    T = _rw(500, 15)
+    for m in (8, 40):
+        mp, idx = oracle.matrix_profile(T, m)
+        for i in (0, 7, 250, len(T) - m):
+            nn, j = oracle.nn_one(T, m, i)
+            assert nn == pytest.approx(mp[i], rel=1e-14)
+            assert oracle.dist(T, m, i, j) == pytest.approx(mp[i], rel=1e-12)
+
+
 def test_profile_exact_repetition_is_zero():
     rng = np.random.default_rng(9)
     pat = rng.standard_normal(37)
