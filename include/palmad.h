@@ -107,21 +107,31 @@ typedef struct {
     int64_t survivors;          /* candidates handed from select to refine (sum) */
     int64_t discords;           /* range discords at the final r (sum over lengths) */
     double max_fp32_rho_err;    /* max |rho_fast - rho_fp64| seen on re-checked pairs */
-    /* profile == 1: per-kernel totals (index = palmad_kernel_id) */
-    int64_t launches[8];
-    double kernel_ms[8];
+    double select_flops;        /* algorithmic FP32 work of select: 5 per valid pair
+                                   (2 FMA diagonal update + 1 scale) + 2m per top-row seed */
+    double refine_flops;        /* direct-form refine: 2m per evaluated pair */
+    double sweep_flops;         /* recurrence-form refine: 5 per evaluated pair + 2m per
+                                   direct dot product (top-row and first-column seeds) */
+    /* per-kernel launch counts (always) and summed event times in ms
+       (profile == 1 only); index = PALMAD_K_* */
+    int64_t launches[12];
+    double kernel_ms[12];
 } palmad_stats;
 
 /* Kernel ids for palmad_stats.launches / kernel_ms. */
 enum {
-    PALMAD_K_STATS = 0,   /* window statistics init / Eq. 7-8 advance */
-    PALMAD_K_SELECT = 1,  /* candidate select (Algorithm 3) */
-    PALMAD_K_COMPACT = 2, /* bitmap -> survivor list (Algorithm 4 line 2) */
-    PALMAD_K_REFINE = 3,  /* refine, fast pass (Algorithm 4) */
-    PALMAD_K_RECHECK = 4, /* refine, FP64 re-check of the near-minimum pairs */
-    PALMAD_K_TOPK = 5,    /* discord gather + per-length top-K */
-    PALMAD_K_HEAT = 6,    /* heatmap row write (Eq. 10) */
-    PALMAD_K_OTHER = 7
+    PALMAD_K_STATS = 0,         /* window statistics init / Eq. 7-8 advance */
+    PALMAD_K_SELECT = 1,        /* candidate select (Algorithm 3) */
+    PALMAD_K_COMPACT = 2,       /* bitmap -> survivor list (Algorithm 4 line 2) */
+    PALMAD_K_PLAN = 3,          /* survivor split (sweep / direct) + centred windows */
+    PALMAD_K_REFINE_SWEEP = 4,  /* refine, recurrence form over dense strips (Algorithm 4) */
+    PALMAD_K_REFINE_DIRECT = 5, /* refine, direct form over scattered survivors */
+    PALMAD_K_RECHECK = 6,       /* FP64 re-check of the near-minimum pairs */
+    PALMAD_K_GATHER = 7,        /* range discords of the call */
+    PALMAD_K_TOPK = 8,          /* per-length top-K */
+    PALMAD_K_HEAT = 9,          /* heatmap row write (Eq. 10) */
+    PALMAD_K_OTHER = 10,
+    PALMAD_K_COUNT = 12
 };
 
 /* Fills *opt with the defaults (FP32, exclusive top-K, plain form,

@@ -15,9 +15,9 @@ using namespace palmad;
 
 namespace {
 
-constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24, FP32 unit roundoff
 constexpr int kSelectH = 256;                    // rows per select strip (32 lanes x 8)
-constexpr int kDefaultCap = 2048;                // select columns past the strip triangle
+constexpr int kDefaultCap = 512;                 // select columns past the strip triangle
+constexpr int kRefineSeg = 512;                  // refine sweep columns per work item (multiple of 256)
 constexpr int kMaxTopK = 1024;
 
 template <class T>
@@ -28,16 +28,20 @@ struct DBuf {
 
 // Small device-side counters, reset per DRAG call (flags persist per length).
 struct Small {
-    int32_t work[4];          // 0 select, 1 refine
+    int32_t work[4];          // 0 select, 1 direct refine, 2 sweep refine
     int32_t nsurv;
     int32_t dcount;
     uint32_t maxerr;
-    int32_t pad;
-    unsigned long long pairs[4];  // 0 select, 1 refine, 2 fp64
+    int32_t nref;             // strips swept by refine (this batch)
+    int32_t ndirect;          // survivors refined by the direct form (this batch)
+    int32_t pad[3];
+    unsigned long long pairs[8];  // 0 select, 1 direct refine, 2 fp64, 3 select seeds,
+                                  // 4 sweep refine, 5 sweep refine seeds
 };
 struct Flags {
     int32_t flags;  // |1 non-finite, |2 flat window at the current length
-    int32_t pad[3];
+    uint32_t ab[2]; // max |df| inv, max |dg| inv over the windows (float bits)
+    int32_t pad;
 };
 
 struct Timing {
@@ -58,8 +62,9 @@ struct palmad_ctx {
     DBuf<double> mu[2], var[2];
     DBuf<float4> win;
     DBuf<uint32_t> bits, bits0;
-    DBuf<int32_t> surv;
-    DBuf<float> acen, asum, tilemax;
+    DBuf<int32_t> surv, slot_of, strips, direct;
+    DBuf<float> acen, asum, cmax;
+    DBuf<int32_t> scount;
     DBuf<uint32_t> gmax;
     DBuf<int32_t> dead;
     DBuf<unsigned long long> nn2;
@@ -132,6 +137,7 @@ void release(DBuf<T>& b) {
 palmad_status tbegin(palmad_ctx* ctx, int kid, Timing& t) {
     t.kid = kid;
     t.a = t.b = nullptr;
+    ctx->stats.launches[kid] += 1;
     if (!ctx->profile) return PALMAD_OK;
     for (cudaEvent_t* e : {&t.a, &t.b}) {
         if (!ctx->ev_free.empty()) {
@@ -156,10 +162,7 @@ palmad_status tend(palmad_ctx* ctx, Timing& t) {
 void tcollect(palmad_ctx* ctx) {
     for (Timing& t : ctx->timings) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
-            ctx->stats.kernel_ms[t.kid] += ms;
-            ctx->stats.launches[t.kid] += 1;
-        }
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) ctx->stats.kernel_ms[t.kid] += ms;
         ctx->ev_free.push_back(t.a);
         ctx->ev_free.push_back(t.b);
     }
@@ -210,7 +213,7 @@ struct Job {
     int32_t m = 0;     // current length
     int32_t refine_cap = 0;
     int32_t kpad_max = 0;
-    int32_t ntiles_max = 0;
+    int32_t nchunks_max = 0;
 };
 
 palmad_status reserve(palmad_ctx* ctx, Job& job) {
@@ -224,6 +227,8 @@ palmad_status reserve(palmad_ctx* ctx, Job& job) {
     CKS(ensure(ctx, ctx->bits, Pmax));
     CKS(ensure(ctx, ctx->bits0, Pmax));
     CKS(ensure(ctx, ctx->surv, Nmax));
+    CKS(ensure(ctx, ctx->slot_of, Nmax));
+    CKS(ensure(ctx, ctx->strips, (Nmax + kSelectH - 1) / kSelectH));
     CKS(ensure(ctx, ctx->didx, Nmax));
     CKS(ensure(ctx, ctx->dnn, Nmax));
     CKS(ensure(ctx, ctx->pidx, kMaxTopK));
@@ -231,15 +236,17 @@ palmad_status reserve(palmad_ctx* ctx, Job& job) {
     CKS(ensure(ctx, ctx->small, 1));
     CKS(ensure(ctx, ctx->flags, 1));
     job.kpad_max = ((job.maxL + 31) / 32) * 32;
-    job.ntiles_max = int32_t((Nmax + 255) / 256);
-    // survivors refined per batch: bounded by the per-tile max table (<= 256 MB)
-    int64_t cap = (int64_t(1) << 26) / std::max(1, job.ntiles_max);
+    job.nchunks_max = int32_t((Nmax + 31) / 32);
+    // survivors refined per batch: bounded by the per-chunk max table (<= 256 MB)
+    int64_t cap = (int64_t(1) << 26) / std::max(1, job.nchunks_max);
     cap = std::min<int64_t>(cap, 16384);
     cap = std::max<int64_t>(64, (cap / 64) * 64);
     job.refine_cap = int32_t(cap);
     CKS(ensure(ctx, ctx->acen, size_t(cap) * job.kpad_max));
     CKS(ensure(ctx, ctx->asum, size_t(cap)));
-    CKS(ensure(ctx, ctx->tilemax, size_t(cap) * job.ntiles_max));
+    CKS(ensure(ctx, ctx->direct, size_t(cap)));
+    CKS(ensure(ctx, ctx->cmax, size_t(cap) * job.nchunks_max));
+    CKS(ensure(ctx, ctx->scount, (Nmax + kSelectH - 1) / kSelectH + 1));
     CKS(ensure(ctx, ctx->gmax, size_t(cap)));
     CKS(ensure(ctx, ctx->dead, size_t(cap)));
     CKS(ensure(ctx, ctx->nn2, size_t(cap)));
@@ -276,6 +283,7 @@ palmad_status prepare_length(palmad_ctx* ctx, Job& job, int32_t m, bool first) {
     a.win = ctx->win.p;
     a.bits = ctx->bits0.p;
     a.flags = &ctx->flags.p->flags;
+    a.ab = ctx->flags.p->ab;
     LAUNCH(PALMAD_K_STATS, launch_stats_step(a, ctx->stream));
     job.m = m;
     if (first) {
@@ -302,25 +310,29 @@ palmad_status drag_call(palmad_ctx* ctx, Job& job, double r, DragResult& out) {
     const double rho_thr = 1.0 - r2 / (2.0 * m);
     const double band = job.opt.band_rel * r2 / m;
     const int64_t cap = job.opt.select_cap > 0 ? job.opt.select_cap : kDefaultCap;
-    const double eps_sel = (4.0 * double(kSelectH + cap + 64) + 3.0 * m + 64.0) * kU32;
-    const double eps_ref = (4.0 * m + 128.0) * kU32;
-    const float prune_sel = r > 0.0 ? float(rho_thr + std::max(eps_sel, band)) : kInf;
-    const float prune_ref = r > 0.0 ? float(rho_thr + std::max(eps_ref, band)) : kInf;
+    Thresh th{};
+    th.rho_thr = float(rho_thr);
+    th.band = float(band);
+    th.prune = r > 0.0 ? 1 : 0;
+    th.m = m;
+    th.H = kSelectH;
+    th.ab = ctx->flags.p->ab;
 
     CK(cudaMemsetAsync(ctx->small.p, 0, sizeof(Small), ctx->stream));
     CK(cudaMemcpyAsync(ctx->bits.p, ctx->bits0.p, P * sizeof(uint32_t), cudaMemcpyDeviceToDevice, ctx->stream));
 
-    SelectArgs sa{};
+    SweepArgs sa{};
     sa.T = job.T;
     sa.n = n;
     sa.N = N;
     sa.m = m;
     sa.win = ctx->win.p;
-    sa.bits = ctx->bits.p;
-    sa.rho_prune = prune_sel;
-    sa.cap = cap;
+    sa.th = th;
     sa.work = &ctx->small.p->work[0];
     sa.pairs = &ctx->small.p->pairs[0];
+    sa.seeds = &ctx->small.p->pairs[3];
+    sa.bits = ctx->bits.p;
+    sa.cap = cap;
     if (r > 0.0) LAUNCH(PALMAD_K_SELECT, launch_select(sa, ctx->sel_grid, ctx->stream));
 
     CompactArgs ca{ctx->bits.p, N, ctx->surv.p, &ctx->small.p->nsurv};
@@ -332,17 +344,45 @@ palmad_status drag_call(palmad_ctx* ctx, Job& job, double r, DragResult& out) {
     ctx->stats.device_passes += 1;
 
     const int32_t kpad = ((m + 31) / 32) * 32;
-    const int32_t ntiles = int32_t((N + 255) / 256);
+    const int32_t nchunks = int32_t((N + 31) / 32);
+    const int64_t nstrip_all = (N + kSelectH - 1) / kSelectH;
     for (int32_t b0 = 0; b0 < nsurv; b0 += job.refine_cap) {
         const int32_t ns = std::min(job.refine_cap, nsurv - b0);
         const int32_t* surv = ctx->surv.p + b0;
         CK(cudaMemsetAsync(ctx->gmax.p, 0, ns * sizeof(uint32_t), ctx->stream));
         CK(cudaMemsetAsync(ctx->dead.p, 0, ns * sizeof(int32_t), ctx->stream));
         CK(cudaMemsetAsync(ctx->nn2.p, 0x7f, ns * sizeof(unsigned long long), ctx->stream));
-        CK(cudaMemsetAsync(&ctx->small.p->work[1], 0, sizeof(int32_t), ctx->stream));
-        LAUNCH(PALMAD_K_REFINE,
+        CK(cudaMemsetAsync(ctx->slot_of.p, 0xff, N * sizeof(int32_t), ctx->stream));
+        CK(cudaMemsetAsync(&ctx->small.p->work[1], 0, 2 * sizeof(int32_t), ctx->stream));
+        CK(cudaMemsetAsync(&ctx->small.p->nref, 0, 2 * sizeof(int32_t), ctx->stream));
+        CK(cudaMemsetAsync(ctx->scount.p, 0, nstrip_all * sizeof(int32_t), ctx->stream));
+        const int32_t thr = std::max(2, (5 * kSelectH + m + m - 1) / m);
+        LAUNCH(PALMAD_K_PLAN, launch_plan(surv, ns, ctx->win.p, kSelectH, thr, ctx->slot_of.p, ctx->scount.p, ctx->strips.p,
+                                            &ctx->small.p->nref, ctx->direct.p, &ctx->small.p->ndirect, ctx->stream));
+        LAUNCH(PALMAD_K_PLAN,
                launch_refine_prep(job.T, ctx->win.p, surv, ns, m, kpad, ctx->acen.p, ctx->asum.p, ctx->stream));
+        SweepArgs wa{};
+        wa.T = job.T;
+        wa.n = n;
+        wa.N = N;
+        wa.m = m;
+        wa.win = ctx->win.p;
+        wa.th = th;
+        wa.work = &ctx->small.p->work[2];
+        wa.pairs = &ctx->small.p->pairs[4];
+        wa.seeds = &ctx->small.p->pairs[5];
+        wa.strips = ctx->strips.p;
+        wa.nref = &ctx->small.p->nref;
+        wa.seg = kRefineSeg;
+        wa.slot_of = ctx->slot_of.p;
+        wa.dead = ctx->dead.p;
+        wa.gmax = ctx->gmax.p;
+        wa.cmax = ctx->cmax.p;
+        wa.nchunks = nchunks;
+        LAUNCH(PALMAD_K_REFINE_SWEEP, launch_refine_sweep(wa, ctx->sel_grid, ctx->stream));
         RefineArgs ra{};
+        ra.list = ctx->direct.p;
+        ra.nlist = &ctx->small.p->ndirect;
         ra.T = job.T;
         ra.n = n;
         ra.N = N;
@@ -353,15 +393,15 @@ palmad_status drag_call(palmad_ctx* ctx, Job& job, double r, DragResult& out) {
         ra.ns = ns;
         ra.acen = ctx->acen.p;
         ra.asum = ctx->asum.p;
-        ra.rho_prune = prune_ref;
-        ra.ntiles = ntiles;
+        ra.th = th;
+        ra.nchunks = nchunks;
         ra.gmax = ctx->gmax.p;
         ra.dead = ctx->dead.p;
-        ra.tilemax = ctx->tilemax.p;
+        ra.cmax = ctx->cmax.p;
         ra.flags = &ctx->flags.p->flags;
         ra.work = &ctx->small.p->work[1];
         ra.pairs = &ctx->small.p->pairs[1];
-        LAUNCH(PALMAD_K_REFINE, launch_refine(ra, ctx->ref_grid, ctx->stream));
+        LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine(ra, ctx->ref_grid, ctx->stream));
         RecheckArgs rc{};
         rc.T = job.T;
         rc.n = n;
@@ -376,16 +416,16 @@ palmad_status drag_call(palmad_ctx* ctx, Job& job, double r, DragResult& out) {
         rc.acen = ctx->acen.p;
         rc.gmax = ctx->gmax.p;
         rc.dead = ctx->dead.p;
-        rc.tilemax = ctx->tilemax.p;
-        rc.ntiles = ntiles;
-        rc.eps2 = float(2.0 * eps_ref);
+        rc.cmax = ctx->cmax.p;
+        rc.nchunks = nchunks;
+        rc.th = th;
         rc.nn2 = ctx->nn2.p;
         rc.flags = &ctx->flags.p->flags;
         rc.pairs = &ctx->small.p->pairs[2];
         rc.maxerr = &ctx->small.p->maxerr;
         LAUNCH(PALMAD_K_RECHECK, launch_recheck(rc, ctx->stream));
         GatherArgs ga{surv, ns, ctx->dead.p, ctx->nn2.p, r, ctx->didx.p, ctx->dnn.p, &ctx->small.p->dcount};
-        LAUNCH(PALMAD_K_TOPK, launch_gather(ga, ctx->stream));
+        LAUNCH(PALMAD_K_GATHER, launch_gather(ga, ctx->stream));
     }
     TopkArgs ta{ctx->didx.p, ctx->dnn.p, &ctx->small.p->dcount, job.K, m, job.exclusive ? 1 : 0, ctx->pidx.p,
                 ctx->pnn.p};
@@ -397,6 +437,10 @@ palmad_status drag_call(palmad_ctx* ctx, Job& job, double r, DragResult& out) {
     const Small& sm = *ctx->h_small;
     ctx->stats.select_pairs += int64_t(sm.pairs[0]);
     ctx->stats.refine_pairs += int64_t(sm.pairs[1]);
+    ctx->stats.refine_pairs += int64_t(sm.pairs[4]);
+    ctx->stats.select_flops += 5.0 * double(sm.pairs[0]) + 2.0 * m * double(sm.pairs[3]);
+    ctx->stats.refine_flops += 2.0 * m * double(sm.pairs[1]);
+    ctx->stats.sweep_flops += 5.0 * double(sm.pairs[4]) + 2.0 * m * double(sm.pairs[5]);
     ctx->stats.fp64_pairs += int64_t(sm.pairs[2]);
     {
         uint32_t e = sm.maxerr;
@@ -562,7 +606,7 @@ palmad_status palmad_create(palmad_ctx** out, int device, void* cuda_stream) {
     if (cudaMallocHost(&ctx->h_flags, sizeof(Flags)) != cudaSuccess) return bail(PALMAD_ERR_OOM);
     if (cudaMallocHost(&ctx->h_pidx, kMaxTopK * sizeof(int64_t)) != cudaSuccess) return bail(PALMAD_ERR_OOM);
     if (cudaMallocHost(&ctx->h_pnn, kMaxTopK * sizeof(double)) != cudaSuccess) return bail(PALMAD_ERR_OOM);
-    ctx->sel_grid = select_grid(device);
+    ctx->sel_grid = sweep_grid(device);
     ctx->ref_grid = refine_grid(device);
     reset_stats(ctx);
     *out = ctx;
@@ -582,9 +626,13 @@ void palmad_destroy(palmad_ctx* ctx) {
     release(ctx->bits);
     release(ctx->bits0);
     release(ctx->surv);
+    release(ctx->slot_of);
+    release(ctx->strips);
+    release(ctx->direct);
     release(ctx->acen);
     release(ctx->asum);
-    release(ctx->tilemax);
+    release(ctx->cmax);
+    release(ctx->scount);
     release(ctx->gmax);
     release(ctx->dead);
     release(ctx->nn2);
@@ -627,6 +675,13 @@ palmad_status palmad_find_discords_device(palmad_ctx* ctx, const float* T_dev, i
     palmad_options o;
     CKS(read_options(ctx, opt, o));
     CKS(begin_call(ctx, o));
+    // The sweeps copy the series with 16-byte asynchronous copies: stage a
+    // series that does not start on a 16-byte boundary.
+    if (reinterpret_cast<uintptr_t>(T_dev) % 16 != 0) {
+        CKS(ensure(ctx, ctx->T, size_t(n)));
+        CK(cudaMemcpyAsync(ctx->T.p, T_dev, size_t(n) * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+        T_dev = ctx->T.p;
+    }
     Job job{};
     job.T = T_dev;
     job.n = n;
@@ -723,7 +778,10 @@ palmad_status palmad_find_discords_batch(palmad_ctx* ctx, int32_t count, const f
         total.survivors += st.survivors;
         total.discords += st.discords;
         total.max_fp32_rho_err = std::max(total.max_fp32_rho_err, st.max_fp32_rho_err);
-        for (int k = 0; k < 8; ++k) {
+        total.select_flops += st.select_flops;
+        total.refine_flops += st.refine_flops;
+        total.sweep_flops += st.sweep_flops;
+        for (int k = 0; k < PALMAD_K_COUNT; ++k) {
             total.launches[k] += st.launches[k];
             total.kernel_ms[k] += st.kernel_ms[k];
         }

@@ -76,6 +76,7 @@ __global__ void k_stats_step(const StatsArgs a) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     const int32_t m = a.m;
     bool any_flat = false;
+    float amax = 0.f, bmax = 0.f;
     for (int64_t i = tid; i < N; i += stride) {
         double mu_i, var_i;
         const float t_add = a.T[i + m - 1];
@@ -88,15 +89,25 @@ __global__ void k_stats_step(const StatsArgs a) {
         any_flat |= flat;
         float df = 0.f, dg = 0.f;
         if (i >= 1) {
-            double mu_p, var_p;
-            const float t_rm = a.T[i - 1];
-            if (a.advance) advance_one(a.mu_old[i - 1], a.var_old[i - 1], a.T[i + m - 2], m, mu_p, var_p);
-            else mu_p = a.mu_old[i - 1];
-            df = float(0.5 * (double(t_add) - double(t_rm)));
-            dg = float((double(t_add) - mu_i) + (double(t_rm) - mu_p));
+            // mu_{i-1} = mu_i - (t[i+m-1] - t[i-1]) / m for windows of one length
+            const double diff = double(t_add) - double(a.T[i - 1]);
+            const double mu_p = mu_i - diff / double(m);
+            df = float(0.5 * diff);
+            dg = float((double(t_add) - mu_i) + (double(a.T[i - 1]) - mu_p));
         }
-        const float inv = flat ? 0.f : float(1.0 / (sqrt(double(m)) * sd));
+        const float inv = flat ? 0.f : rsqrtf(float(double(m) * var_i));
         a.win[i] = make_float4(df, dg, inv, float(mu_i));
+        amax = fmaxf(amax, fabsf(df) * inv);
+        bmax = fmaxf(bmax, fabsf(dg) * inv);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&a.ab[0], __float_as_uint(amax));
+        atomicMax(&a.ab[1], __float_as_uint(bmax));
     }
     // Candidate bitmap: a window starts alive iff it has a non-self match.
     for (int64_t w = tid; w < P; w += stride) {

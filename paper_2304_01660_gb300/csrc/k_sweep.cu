@@ -1,0 +1,393 @@
+// Strip sweeps: candidate select (DRAG phase 1; Algorithm 3, Sec. 3.2) and
+// the recurrence form of refine (DRAG phase 2; Algorithm 4, Sec. 3.3).
+//
+// A warp owns a strip of H = 32*D consecutive windows (rows i) and steps
+// across a range of windows (columns j), 32 columns per chunk:
+//   * lane l holds rows i0 + l*D .. i0 + l*D + D-1 in registers; one step
+//     advances every row by one column with the diagonal recurrence of Eq. 9
+//     (cov(i,j) = cov(i-1,j-1) + df_i dg_j + df_j dg_i); the value of the row
+//     above arrives from the previous lane by one shuffle;
+//   * the strip's top row has no row above: its dot products ("QTrow" of
+//     Algorithm 3) are computed per chunk by a transposed register-blocked
+//     pass over the staged series, then reduce-scattered so that lane l
+//     holds column c0 + l;
+//   * select scans to the right (j >= i + m) from the strip's triangle, as
+//     the paper's segment-scans-right; a pair with rho > rho_prune (d < r
+//     beyond the FP32 error band) clears the row's and the column's
+//     candidate bit (Cand and Neighbor of Algorithm 3 are one bitmap here,
+//     since refine ANDs them anyway); the warp leaves the strip once every
+//     row is dead (Algorithm 3 lines 14-15) or after `cap` columns;
+//   * refine sweeps a 2048-column segment of every strip that holds enough
+//     survivors (both sides of the exclusion zone |i - j| < m, which is
+//     masked), starting from directly computed first-column dot products;
+//     per survivor it records the maximum rho of every 32-column chunk, and
+//     a pair with rho > rho_prune marks the survivor dead (the early abandon
+//     of Algorithm 4).
+// Pruning is sound: a pair is used only when its FP32 rho exceeds the exact
+// threshold by more than the error bound, so no range discord is dropped.
+#include "palmad_dev.cuh"
+
+namespace palmad {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarpsPerCta = 4;
+
+struct WarpSmem {
+    float* ahat;    // [kp]         centred top-row window, zero padded
+    float* tw;      // [2][kp + 32] series slices of this and the next chunk
+    float4* colrec; // [2][32]      column records of this and the next chunk
+    float* seed;    // [32]         top-row dot products of this chunk
+};
+
+__device__ __forceinline__ size_t warp_smem_floats(int kp) { return size_t(kp) + 2 * (kp + 32) + 2 * 128 + 32; }
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Start the asynchronous copy of chunk c0's series slice and column records
+// into buffer b (zero fill past the ends of T and of the windows).  T and
+// win are 16-byte aligned and c0 is a multiple of 32.
+__device__ __forceinline__ void issue_chunk(const SweepArgs& a, const WarpSmem& sm, int b, int64_t c0, int kp,
+                                            int lane) {
+    float* tw = sm.tw + b * (kp + 32);
+    for (int x = lane * 4; x < kp + 32; x += 128) {
+        const int64_t t = c0 + x;
+        const int64_t rem = a.n - t;
+        const int bytes = rem >= 4 ? 16 : (rem > 0 ? int(rem) * 4 : 0);
+        cp_async16(tw + x, bytes > 0 ? static_cast<const void*>(a.T + t) : static_cast<const void*>(a.T), bytes);
+    }
+    const int64_t j = c0 + lane;
+    cp_async16(sm.colrec + b * 32 + lane, j < a.N ? static_cast<const void*>(a.win + j) : static_cast<const void*>(a.win),
+               j < a.N ? 16 : 0);
+    cp_async_commit();
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Sum over lanes of acc[c] lands in lane c (reduce-scatter, 31 shuffles).
+__device__ __forceinline__ float reduce_scatter32(float (&acc)[32], int lane) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < o; ++k) {
+            const float send = upper ? acc[k] : acc[k + o];
+            const float keep = upper ? acc[k + o] : acc[k];
+            acc[k] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+    return acc[0];
+}
+
+// Top-row dot products cov(top, c0 + lane) of one chunk from the staged
+// buffer b (series slice minus the offset b0 = mu of column c0).
+__device__ __forceinline__ void chunk_seeds(const SweepArgs& a, const WarpSmem& sm, int b, int64_t c0, float suma,
+                                            int kp, int lane) {
+    const int s4 = kp / 32;
+    float* tw = sm.tw + b * (kp + 32);
+    const float4* cr = sm.colrec + b * 32;
+    const float b0 = cr[0].w;
+    for (int x = lane; x < kp + 32; x += 32) tw[x] -= b0;
+    __syncwarp();
+    float acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+    const int kl = lane * s4;
+    for (int q = 0; q < s4; q += 4) {
+        const float4 av = *reinterpret_cast<const float4*>(sm.ahat + kl + q);
+        const float a4[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+        for (int cb = 0; cb < 4; ++cb) {
+            const float* tp = tw + kl + q + cb * 8;
+            const float4 t0 = *reinterpret_cast<const float4*>(tp);
+            const float4 t1 = *reinterpret_cast<const float4*>(tp + 4);
+            const float4 t2 = *reinterpret_cast<const float4*>(tp + 8);
+            const float tv[12] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x, t2.y, t2.z, t2.w};
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) acc[cb * 8 + cc] = fmaf(a4[qq], tv[qq + cc], acc[cb * 8 + cc]);
+        }
+    }
+    const float dot = reduce_scatter32(acc, lane);
+    const int64_t j = c0 + lane;
+    sm.seed[lane] = (j < a.N) ? dot - (cr[lane].w - b0) * suma : 0.f;
+    __syncwarp();
+}
+
+// cov(r0 + d, ja) for d < D: direct dot products of this lane's rows with
+// column ja (centred column window x, rows offset by b0 = mu of row r0).
+template <int D>
+__device__ __forceinline__ void first_col_seeds(const SweepArgs& a, int64_t r0, int64_t ja, float (&cov)[D]) {
+    const int32_t m = a.m;
+    const float mux = a.win[ja].w;
+    const float b0 = (r0 < a.N) ? a.win[r0].w : 0.f;
+    float acc[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) acc[d] = 0.f;
+    float sx = 0.f;
+    for (int k = 0; k < m; k += 8) {
+        float x[8], y[D + 8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t t = ja + k + q;
+            x[q] = (k + q < m && t < a.n) ? (a.T[t] - mux) : 0.f;
+            sx += x[q];
+        }
+#pragma unroll
+        for (int q = 0; q < D + 8; ++q) {
+            const int64_t t = r0 + k + q;
+            y[q] = (t < a.n) ? (a.T[t] - b0) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int d = 0; d < D; ++d) acc[d] = fmaf(x[q], y[d + q], acc[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const int64_t i = r0 + d;
+        const float mui = (i < a.N) ? a.win[i].w : 0.f;
+        cov[d] = acc[d] - (mui - b0) * sx;
+    }
+}
+
+template <int D, bool REFINE>
+__global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const SweepArgs a) {
+    constexpr int H = 32 * D;
+    extern __shared__ __align__(16) float smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int32_t m = a.m;
+    const int kp = ((m + 127) / 128) * 128;
+    float* base = smem + warp_smem_floats(kp) * wid;
+    const WarpSmem sm{base, base + kp, reinterpret_cast<float4*>(base + kp + 2 * (kp + 32)),
+                      base + kp + 2 * (kp + 32) + 256};
+
+    const int64_t N = a.N;
+    const float rho_prune = rho_prune_of(a.th);
+    const int64_t nstrips = (N + H - 1) / H;
+    const int64_t nseg = REFINE ? (N + a.seg - 1) / a.seg : 1;
+    const int64_t nitems = REFINE ? int64_t(*a.nref) * nseg : nstrips;
+    unsigned long long pairs = 0, seeds = 0;
+
+    for (;;) {
+        int64_t item = 0;
+        if (lane == 0) item = atomicAdd(a.work, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= nitems) break;
+        int64_t s, ja, jb;
+        if (REFINE) {
+            s = a.strips[item / nseg];
+            ja = (item % nseg) * a.seg;
+            jb = min64(N, ja + a.seg);
+        } else {
+            s = item;
+            ja = s * H + m;
+            if (ja >= N) continue;  // no window to the right: column marks / refine decide these rows
+            jb = min64(N, s * H + H - 1 + m + a.cap);
+        }
+        const int64_t i0 = s * H;
+        const int64_t r0 = i0 + int64_t(lane) * D;
+
+        // Rows of this lane.
+        float df_r[D], dg_r[D], inv_r[D], thr_r[D], cov[D], rmax[D];
+        int32_t slot[D];
+        uint32_t alive = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int64_t i = r0 + d;
+            float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < N) rec = a.win[i];
+            df_r[d] = rec.x;
+            dg_r[d] = rec.y;
+            inv_r[d] = rec.z;
+            thr_r[d] = (i >= N) ? kInf : (rec.z > 0.f ? rho_prune / rec.z : (rho_prune < 0.f ? -kInf : kInf));
+            cov[d] = 0.f;
+            rmax[d] = -kInf;
+            slot[d] = -1;
+            if (REFINE && i < N) {
+                slot[d] = a.slot_of[i];
+                if (slot[d] >= 0 && !__ldcg(&a.dead[slot[d]])) alive |= 1u << d;
+            }
+        }
+        const int64_t wrd = r0 >> 5;
+        const int sh = int(r0 & 31);
+        const uint32_t dmask = (D == 32) ? kFull : ((1u << D) - 1u);
+        if (!REFINE) alive = (r0 < N) ? ((__ldcg(&a.bits[wrd]) >> sh) & dmask) : 0u;
+        if (!__any_sync(kFull, alive)) continue;
+
+        const int64_t cfirst = ja & ~int64_t(31);
+        issue_chunk(a, sm, 0, cfirst, kp, lane);
+
+        // Centred top-row window and its sum (FP32; the sum absorbs the
+        // rounding of mu so the seed correction is exact to rounding).
+        const float mu_top = a.win[i0].w;
+        float part = 0.f;
+        for (int k = lane; k < kp; k += 32) {
+            const float v = (k < m) ? (a.T[i0 + k] - mu_top) : 0.f;
+            sm.ahat[k] = v;
+            part += v;
+        }
+        const float suma = warp_sum(part);
+        __syncwarp();
+
+        float tmax[D];
+        if (REFINE) {
+            first_col_seeds<D>(a, r0, ja, cov);
+#pragma unroll
+            for (int d = 0; d < D; ++d) tmax[d] = -kInf;
+            seeds += H;
+        }
+        const int64_t rows = min64(H, N - i0);
+
+        int buf = 0;
+        for (int64_t c0 = cfirst; c0 < jb; c0 += 32, buf ^= 1) {
+            cp_async_wait_all();
+            __syncwarp();
+            if (c0 + 32 < jb) issue_chunk(a, sm, buf ^ 1, c0 + 32, kp, lane);
+            // state other warps may have changed, read early and used at the chunk end
+            uint32_t gbits = 0, gdead = 0;
+            if (!REFINE && r0 < N) gbits = __ldcg(&a.bits[wrd]);
+            if (REFINE) {
+#pragma unroll
+                for (int d = 0; d < D; ++d)
+                    if (((alive >> d) & 1u) && __ldcg(&a.dead[slot[d]])) gdead |= 1u << d;
+            }
+            chunk_seeds(a, sm, buf, c0, suma, kp, lane);
+            const float4* crb = sm.colrec + buf * 32;
+            const int steps = int(min64(32, jb - c0));
+            const int st0 = int(max64(0, ja - c0));
+            bool masked;
+            if (REFINE) masked = !(c0 >= i0 + H - 1 + m || c0 + 31 <= i0 - m);
+            else masked = (c0 - ja) < int64_t(H - 1);
+            uint32_t colmask = 0;
+            for (int st = st0; st < steps; ++st) {
+                const int64_t j = c0 + st;
+                const float4 cr = crb[st];
+                const float sd = sm.seed[st];
+                const float up = __shfl_up_sync(kFull, cov[D - 1], 1);
+                if (!REFINE || j != ja) {
+#pragma unroll
+                    for (int d = D - 1; d >= 1; --d) cov[d] = fmaf(df_r[d], cr.y, fmaf(cr.x, dg_r[d], cov[d - 1]));
+                    cov[0] = (lane == 0) ? sd : fmaf(df_r[0], cr.y, fmaf(cr.x, dg_r[0], up));
+                }
+                bool pred = false;
+                if (masked) {
+                    const int64_t lim = j - r0;  // j - i for d = 0
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        float x = cov[d] * cr.z;
+                        const int64_t dj = lim - d;  // j - i
+                        const bool ok = REFINE ? (dj >= m || dj <= -int64_t(m)) : (dj >= m);
+                        x = ok ? x : -kInf;
+                        rmax[d] = fmaxf(rmax[d], x);
+                        if (!REFINE) pred |= x > thr_r[d];
+                    }
+                } else {
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        const float x = cov[d] * cr.z;
+                        rmax[d] = fmaxf(rmax[d], x);
+                        if (!REFINE) pred |= x > thr_r[d];
+                    }
+                }
+                if (!REFINE && pred) colmask |= 1u << st;
+            }
+            if (lane == 0) {
+                seeds += 32;
+                if (REFINE) pairs += uint64_t(rows) * uint64_t(steps - st0);
+                else
+                    for (int st = st0; st < steps; ++st) {
+                        const int64_t v = min64(rows, c0 + st - ja + 1);
+                        if (v > 0) pairs += uint64_t(v);
+                    }
+            }
+            if (!REFINE) {
+                // Neighbour (column) marks, row deaths, rows killed elsewhere.
+                const uint32_t cw = __reduce_or_sync(kFull, colmask);
+                if (lane == 0 && cw) atomicAnd(&a.bits[c0 >> 5], ~cw);
+                uint32_t newdead = 0;
+#pragma unroll
+                for (int d = 0; d < D; ++d)
+                    if (((alive >> d) & 1u) && rmax[d] > thr_r[d]) newdead |= 1u << d;
+                if (newdead) {
+                    alive &= ~newdead;
+                    atomicAnd(&a.bits[wrd], ~(newdead << sh));
+                }
+                if (r0 < N) alive &= (gbits >> sh) & dmask;
+                if (!__any_sync(kFull, alive)) break;
+            } else {
+                // Per-survivor chunk maximum and deaths.
+                const int32_t t = int32_t(c0 >> 5);
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    if (slot[d] >= 0) {
+                        const float rho = rmax[d] > -kInf ? rmax[d] * inv_r[d] : -kInf;
+                        a.cmax[int64_t(slot[d]) * a.nchunks + t] = rho;
+                        tmax[d] = fmaxf(tmax[d], rho);
+                        if (rmax[d] > thr_r[d]) {
+                            a.dead[slot[d]] = 1;
+                            alive &= ~(1u << d);
+                        }
+                    }
+                    rmax[d] = -kInf;
+                }
+                alive &= ~gdead;
+                if (!__any_sync(kFull, alive)) break;
+            }
+            __syncwarp();
+        }
+        cp_async_wait_all();  // no copy may land in a buffer the next item reuses
+        __syncwarp();
+        if (REFINE) {
+#pragma unroll
+            for (int d = 0; d < D; ++d)
+                if (slot[d] >= 0 && tmax[d] > -kInf) atomicMax(&a.gmax[slot[d]], enc_f32(tmax[d]));
+        }
+    }
+    if (lane == 0 && pairs) atomicAdd(a.pairs, pairs);
+    if (lane == 0 && seeds) atomicAdd(a.seeds, seeds);
+}
+
+size_t sweep_smem(int32_t m) {
+    const size_t kp = ((m + 127) / 128) * 128;
+    return sizeof(float) * (kp + 2 * (kp + 32) + 2 * 128 + 32) * kWarpsPerCta;
+}
+
+template <bool REFINE>
+cudaError_t launch_sweep_impl(const SweepArgs& a, int grid, cudaStream_t s) {
+    constexpr int D = 8;
+    const size_t sm = sweep_smem(a.m);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep<D, REFINE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+    }
+    k_sweep<D, REFINE><<<grid, kWarpsPerCta * 32, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int sweep_grid(int device) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return sms * 4;
+}
+
+cudaError_t launch_select(const SweepArgs& a, int grid, cudaStream_t s) { return launch_sweep_impl<false>(a, grid, s); }
+
+cudaError_t launch_refine_sweep(const SweepArgs& a, int grid, cudaStream_t s) {
+    return launch_sweep_impl<true>(a, grid, s);
+}
+
+}  // namespace palmad

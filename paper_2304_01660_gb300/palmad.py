@@ -19,7 +19,8 @@ PALMAD_OK = 0
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NONFINITE", -3: "ERR_OOM", -4: "ERR_CUDA", -5: "ERR_TIMEOUT",
           -6: "ERR_UNSUPPORTED", -7: "ERR_INTERNAL"}
 PREC_FP32, PREC_MIXED = 0, 1
-KERNELS = ["stats", "select", "compact", "refine", "recheck", "topk", "heat", "other"]
+KERNELS = ["stats", "select", "compact", "plan", "refine_sweep", "refine_direct", "recheck", "gather", "topk", "heat",
+           "other", "spare"]
 
 
 class PalmadError(RuntimeError):
@@ -55,14 +56,17 @@ class Stats(ctypes.Structure):
         ("survivors", ctypes.c_int64),
         ("discords", ctypes.c_int64),
         ("max_fp32_rho_err", ctypes.c_double),
-        ("launches", ctypes.c_int64 * 8),
-        ("kernel_ms", ctypes.c_double * 8),
+        ("select_flops", ctypes.c_double),
+        ("refine_flops", ctypes.c_double),
+        ("sweep_flops", ctypes.c_double),
+        ("launches", ctypes.c_int64 * 12),
+        ("kernel_ms", ctypes.c_double * 12),
     ]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("launches", "kernel_ms", "struct_size")}
-        d["launches"] = {KERNELS[i]: int(self.launches[i]) for i in range(8)}
-        d["kernel_ms"] = {KERNELS[i]: float(self.kernel_ms[i]) for i in range(8)}
+        d["launches"] = {KERNELS[i]: int(self.launches[i]) for i in range(12)}
+        d["kernel_ms"] = {KERNELS[i]: float(self.kernel_ms[i]) for i in range(12)}
         return d
 
 

@@ -51,6 +51,19 @@ SERIES = {
 }
 
 
+def _thresholds(mp, qs):
+    """Thresholds at the given quantiles of the profile, each placed midway
+    between two consecutive distinct profile values, so that no window lies
+    within rounding distance of r (d == r is a tie two correct FP64
+    evaluations may break differently)."""
+    v = np.unique(mp[np.isfinite(mp)])
+    out = []
+    for q in qs:
+        k = min(int(q * (len(v) - 1)), len(v) - 2)
+        out.append(0.5 * (v[k] + v[k + 1]))
+    return out
+
+
 def _check_drag(ctx, T, m, r, opts=None):
     gi, gn = ctx.palmad_drag(T, m, r, opts)
     wi, wn = oracle.drag(T, m, r)
@@ -64,9 +77,8 @@ def _check_drag(ctx, T, m, r, opts=None):
 def test_drag_matches_oracle(ctx, name, m):
     T = SERIES[name]()
     mp, _ = oracle.matrix_profile(T, m)
-    fin = mp[np.isfinite(mp)]
-    for q in (0.5, 0.9, 0.99, 1.0):
-        _check_drag(ctx, T, m, float(np.quantile(fin, q)))
+    for r in _thresholds(mp, (0.5, 0.9, 0.99, 1.0)):
+        _check_drag(ctx, T, m, float(r))
 
 
 def test_drag_degenerate_thresholds(ctx):
@@ -91,7 +103,7 @@ def test_drag_n_equals_2m(ctx):
 def test_drag_select_cap_does_not_change_results(ctx, cap):
     T = SERIES["sine4000"]()
     mp, _ = oracle.matrix_profile(T, 50)
-    r = float(np.quantile(mp[np.isfinite(mp)], 0.95))
+    r = float(_thresholds(mp, (0.95,))[0])
     _check_drag(ctx, T, 50, r, _opts(select_cap=cap))
 
 
