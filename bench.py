@@ -183,54 +183,70 @@ def run_ours(args, w):
     ctx = palmad.Context(local, stream.cuda_stream)
     T_dev = torch.from_numpy(T).cuda()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    opt = palmad.palmad_default_options(profile=0 if args.no_events else 1)
+    prof = 0 if args.no_events else 1
+    forms = {"plain": palmad.palmad_default_options(profile=prof),
+             "batched": palmad.palmad_default_options(profile=prof, batch_lengths=args.batch)}
+    best = args.form
 
-    def step():
-        return ctx.palmad_find_discords_device(T_dev, minL, maxL, K, opt)
+    def step(form):
+        return ctx.palmad_find_discords_device(T_dev, minL, maxL, K, forms[form])
 
     ref = None
-    for _ in range(args.warmup):
-        out = step()
-        res = {k: v.cpu().numpy() for k, v in out.items()}
-        if ref is None:
-            ref = res
-        elif not all(np.array_equal(ref[k], res[k]) for k in ref):
-            raise RuntimeError("results differ between runs")
+    for form in forms:
+        for _ in range(args.warmup):
+            out = step(form)
+            res = {k: v.cpu().numpy() for k, v in out.items()}
+            if ref is None:
+                ref = res
+            elif not all(np.array_equal(ref[k], res[k]) for k in ref):
+                raise RuntimeError(f"{form} results differ from the first run")
 
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches = 0
-    kernel_ms = {}
-    flops = {"select": 0.0, "refine_direct": 0.0, "refine_sweep": 0.0}
-    pairs = {"select": 0, "refine": 0, "fp64": 0}
-    with ClockSampler(local) as clk:
-        for s in range(args.steps):
-            flush.zero_()
-            ev[s][0].record(stream)
-            step()
-            ev[s][1].record(stream)
-            st = ctx.palmad_get_stats()
-            launches += sum(st["launches"].values())
-            for k2, v in st["kernel_ms"].items():
-                kernel_ms[k2] = kernel_ms.get(k2, 0.0) + v
-            flops["select"] += st["select_flops"]
-            flops["refine_direct"] += st["refine_flops"]
-            flops["refine_sweep"] += st["sweep_flops"]
-            pairs["select"] += st["select_pairs"]
-            pairs["refine"] += st["refine_pairs"]
-            pairs["fp64"] += st["fp64_pairs"]
+    def timed(form):
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+        if world > 1:
+            dist.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        acc = {"launches": 0, "kernel_ms": {}, "flops": {"select": 0.0, "refine_direct": 0.0, "refine_sweep": 0.0},
+               "pairs": {"select": 0, "refine": 0, "fp64": 0}}
+        with ClockSampler(local) as clk:
+            for s in range(args.steps):
+                flush.zero_()
+                ev[s][0].record(stream)
+                step(form)
+                ev[s][1].record(stream)
+                st = ctx.palmad_get_stats()
+                acc["launches"] += sum(st["launches"].values())
+                for k2, v in st["kernel_ms"].items():
+                    acc["kernel_ms"][k2] = acc["kernel_ms"].get(k2, 0.0) + v
+                acc["flops"]["select"] += st["select_flops"]
+                acc["flops"]["refine_direct"] += st["refine_flops"]
+                acc["flops"]["refine_sweep"] += st["sweep_flops"]
+                acc["pairs"]["select"] += st["select_pairs"]
+                acc["pairs"]["refine"] += st["refine_pairs"]
+                acc["pairs"]["fp64"] += st["fp64_pairs"]
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        tot = sum(a.elapsed_time(b) for a, b in ev)
+        t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        acc["total_ms"] = float(t.item())
+        acc["clocks"] = clk.summary()
+        acc["stats"] = ctx.palmad_get_stats()
+        return acc
+
+    results = {form: timed(form) for form in forms}
+    R = results[best]
+    total_ms = R["total_ms"]
     value = units * args.steps * world / (total_ms / 1e3)
-    last_stats = ctx.palmad_get_stats()
+    last_stats = R["stats"]
+    kernel_ms, flops, pairs, launches = R["kernel_ms"], R["flops"], R["pairs"], R["launches"]
+
+    class _Clk:
+        def summary(self):
+            return R["clocks"]
+    clk = _Clk()
 
     # End to end through the host-pointer entry: upload, all lengths, results.
     T_pin = torch.from_numpy(T).pin_memory()
@@ -241,7 +257,7 @@ def run_ours(args, w):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.palmad_find_discords(T_host, minL, maxL, K)
+        ctx.palmad_find_discords(T_host, minL, maxL, K, forms[best])
         e2e_times.append(time.perf_counter() - t0)
     e2e_t = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -265,7 +281,8 @@ def run_ours(args, w):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "n": n, "minL": minL, "maxL": maxL, "topK": K, "form": "plain-fp32",
+            "config": {"workload": w.name, "n": n, "minL": minL, "maxL": maxL, "topK": K,
+                       "form": f"batched W={args.batch}" if best == "batched" else "plain",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
@@ -277,6 +294,11 @@ def run_ours(args, w):
             "pairs_per_step": {k2: v / args.steps for k2, v in pairs.items()},
             "launches_per_step": launches_per,
             "drag_calls_per_step": last_stats["drag_calls"],
+            "passes_per_step": last_stats["device_passes"],
+            "reruns_per_step": last_stats["reruns"],
+            "forms": {f: {"value": units * args.steps * world / (r["total_ms"] / 1e3), "ms_per_step": r["total_ms"] / args.steps,
+                          "launches_per_step": r["launches"] / args.steps,
+                          "passes_per_step": r["stats"]["device_passes"]} for f, r in results.items()},
             "max_fp32_rho_err": last_stats["max_fp32_rho_err"],
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
         }
@@ -300,6 +322,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end leg")
     ap.add_argument("--no-events", action="store_true", help="no per-launch CUDA events (profiler runs)")
+    ap.add_argument("--form", choices=["plain", "batched"], default="batched", help="form reported as `value`")
+    ap.add_argument("--batch", type=int, default=16, help="lengths per pass of the batched form")
     args = ap.parse_args(argv)
     w = synth.workload(args.workload)
     if args.impl == "reference":

@@ -1,6 +1,21 @@
 // Host driver of libpalmad: context and workspace, the MERLIN threshold
-// schedule (Algorithm 1) and the per-call DRAG orchestration (Algorithms
-// 2-4), behind the C ABI of include/palmad.h.
+// schedule (Algorithm 1), the pass orchestration of DRAG (Algorithms 2-4)
+// and the C ABI of include/palmad.h.
+//
+// A pass evaluates DRAG for a set of lanes (series x length x threshold) in
+// one sequence of launches.  Two schedule forms drive the passes:
+//  * plain:   every DRAG call of Algorithm 1 is a one-lane pass at exactly
+//             the schedule's r;
+//  * batched: after the first five lengths (whose r depends on each single
+//             previous result), W consecutive lengths run as one pass, each
+//             at a speculative r' no larger than the schedule is expected to
+//             reach.  A pass at r' yields every window with nnDist >= r'
+//             exactly, so for any r >= r' the DRAG result at r is its subset
+//             with nnDist >= r, and the greedy top-K at r is the prefix of the
+//             top-K at r' with nnDist >= r.  The host then replays Algorithm 1
+//             exactly, try by try, and reruns a length (as a one-lane pass at a
+//             lower r') only when the schedule needs an r below its r'.
+// Both forms return identical results.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -15,10 +30,10 @@ using namespace palmad;
 
 namespace {
 
-constexpr int kSelectH = 256;                    // rows per select strip (32 lanes x 8)
-constexpr int kDefaultCap = 512;                 // select columns past the strip triangle
-constexpr int kRefineSeg = 512;                  // refine sweep columns per work item (multiple of 256)
-constexpr int kMaxTopK = 1024;
+constexpr int kDefaultCap = 512;     // select columns past the strip triangle
+constexpr int kRefineSeg = 512;      // refine sweep columns per work item (multiple of 256)
+constexpr int kMaxLanes = 4096;      // lanes per pass
+constexpr int64_t kPoolBytes = int64_t(1) << 30;  // per-chunk maxima of the refine pool
 
 template <class T>
 struct DBuf {
@@ -26,27 +41,27 @@ struct DBuf {
     size_t n = 0;
 };
 
-// Small device-side counters, reset per DRAG call (flags persist per length).
+// Counters zeroed per pass.
 struct Small {
-    int32_t work[4];          // 0 select, 1 direct refine, 2 sweep refine
-    int32_t nsurv;
-    int32_t dcount;
-    uint32_t maxerr;
-    int32_t nref;             // strips swept by refine (this batch)
-    int32_t ndirect;          // survivors refined by the direct form (this batch)
-    int32_t pad[3];
-    unsigned long long pairs[8];  // 0 select, 1 direct refine, 2 fp64, 3 select seeds,
-                                  // 4 sweep refine, 5 sweep refine seeds
-};
-struct Flags {
-    int32_t flags;  // |1 non-finite, |2 flat window at the current length
-    uint32_t ab[2]; // max |df| inv, max |dg| inv over the windows (float bits)
-    int32_t pad;
+    int32_t work[8];
+    int32_t nref;
+    int32_t pad[7];
+    unsigned long long pairs[8];
 };
 
 struct Timing {
     int kid;
     cudaEvent_t a, b;
+};
+
+// Device buffers of one lane (one length of one series).
+struct LaneSet {
+    int64_t cap = 0;  // windows
+    DBuf<double> mu, var;
+    DBuf<float4> win;
+    DBuf<uint32_t> bits0, bits;
+    DBuf<int32_t> surv, slot_of, scount, didx;
+    DBuf<double> dnn;
 };
 
 }  // namespace
@@ -56,30 +71,34 @@ struct palmad_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::string err;
-    int sel_grid = 0, ref_grid = 0;
+    int sms = 0;
 
-    DBuf<float> T;
-    DBuf<double> mu[2], var[2];
-    DBuf<float4> win;
-    DBuf<uint32_t> bits, bits0;
-    DBuf<int32_t> surv, slot_of, strips, direct;
-    DBuf<float> acen, asum, cmax;
-    DBuf<int32_t> scount;
-    DBuf<uint32_t> gmax;
-    DBuf<int32_t> dead;
-    DBuf<unsigned long long> nn2;
-    DBuf<int32_t> didx;
-    DBuf<double> dnn;
+    DBuf<float> T;                 // staged series (host entry points)
+    std::vector<LaneSet> sets;
+    // pass
+    DBuf<Lane> lanes;
+    DBuf<LaneState> st;
+    DBuf<int32_t> chain;
+    DBuf<Small> small;
     DBuf<int64_t> pidx;
     DBuf<double> pnn;
-    DBuf<float> heat;
-    DBuf<Small> small;
-    DBuf<Flags> flags;
-
+    Lane* h_lanes = nullptr;
+    LaneState* h_st = nullptr;
+    int32_t* h_chain = nullptr;
     Small* h_small = nullptr;
-    Flags* h_flags = nullptr;
     int64_t* h_pidx = nullptr;
     double* h_pnn = nullptr;
+    int h_cap = 0;                 // lanes the pinned mirrors hold
+    int64_t h_pick_cap = 0;
+    // refine pool
+    int32_t pool = 0;
+    int32_t pool_kpad = 0, pool_nchunks = 0;
+    DBuf<int32_t> slot_lane, slot_win, route, dead;
+    DBuf<float> acen, asum, cmax;
+    DBuf<uint32_t> gmax;
+    DBuf<unsigned long long> nn2;
+    DBuf<int2> strips;
+    DBuf<int32_t> init_flags;
 
     palmad_stats stats{};
     bool profile = false;
@@ -132,6 +151,23 @@ void release(DBuf<T>& b) {
     b.n = 0;
 }
 
+void release_set(LaneSet& s) {
+    release(s.mu); release(s.var); release(s.win); release(s.bits0); release(s.bits);
+    release(s.surv); release(s.slot_of); release(s.scount); release(s.didx); release(s.dnn);
+    s.cap = 0;
+}
+
+palmad_status ensure_set(palmad_ctx* ctx, LaneSet& s, int64_t N) {
+    if (s.cap >= N) return PALMAD_OK;
+    const int64_t P = (N + 31) / 32, S = (N + kStripH - 1) / kStripH + 1;
+    CKS(ensure(ctx, s.mu, N)); CKS(ensure(ctx, s.var, N)); CKS(ensure(ctx, s.win, N));
+    CKS(ensure(ctx, s.bits0, P)); CKS(ensure(ctx, s.bits, P));
+    CKS(ensure(ctx, s.surv, N)); CKS(ensure(ctx, s.slot_of, N)); CKS(ensure(ctx, s.scount, S));
+    CKS(ensure(ctx, s.didx, N)); CKS(ensure(ctx, s.dnn, N));
+    s.cap = N;
+    return PALMAD_OK;
+}
+
 // ------------------------------------------------------------- profiling
 
 palmad_status tbegin(palmad_ctx* ctx, int kid, Timing& t) {
@@ -158,7 +194,6 @@ palmad_status tend(palmad_ctx* ctx, Timing& t) {
     return PALMAD_OK;
 }
 
-// After a stream synchronize: fold recorded launch times into the stats.
 void tcollect(palmad_ctx* ctx) {
     for (Timing& t : ctx->timings) {
         float ms = 0.f;
@@ -197,343 +232,577 @@ palmad_status read_options(palmad_ctx* ctx, const palmad_options* in, palmad_opt
     if (o.precision != PALMAD_PREC_FP32 && o.precision != PALMAD_PREC_MIXED)
         return fail(ctx, PALMAD_ERR_ARG, "unknown precision");
     if (o.select_cap < 0) return fail(ctx, PALMAD_ERR_ARG, "select_cap must be >= 0");
-    if (o.batch_lengths < 0) return fail(ctx, PALMAD_ERR_ARG, "batch_lengths must be >= 0");
+    if (o.batch_lengths < 0 || o.batch_lengths > 1024) return fail(ctx, PALMAD_ERR_ARG, "batch_lengths must lie in [0, 1024]");
     return PALMAD_OK;
 }
 
-// ------------------------------------------------------------ workspace
+// ======================================================== pass execution
 
-struct Job {
-    const float* T;  // device
-    int64_t n;
-    int32_t minL, maxL, K;
-    bool exclusive;
-    palmad_options opt;
-    int cur = 0;       // mu/var buffer holding the current length
-    int32_t m = 0;     // current length
-    int32_t refine_cap = 0;
-    int32_t kpad_max = 0;
-    int32_t nchunks_max = 0;
+struct PassLane {       // host view of one lane request
+    Lane lane;
+    LaneState state;    // uploaded before the pass (flags/ab carried for stats_mode 0)
 };
 
-palmad_status reserve(palmad_ctx* ctx, Job& job) {
-    const int64_t Nmax = job.n - job.minL + 1;
-    const int64_t Pmax = (Nmax + 31) / 32;
-    for (int b = 0; b < 2; ++b) {
-        CKS(ensure(ctx, ctx->mu[b], Nmax));
-        CKS(ensure(ctx, ctx->var[b], Nmax));
-    }
-    CKS(ensure(ctx, ctx->win, Nmax));
-    CKS(ensure(ctx, ctx->bits, Pmax));
-    CKS(ensure(ctx, ctx->bits0, Pmax));
-    CKS(ensure(ctx, ctx->surv, Nmax));
-    CKS(ensure(ctx, ctx->slot_of, Nmax));
-    CKS(ensure(ctx, ctx->strips, (Nmax + kSelectH - 1) / kSelectH));
-    CKS(ensure(ctx, ctx->didx, Nmax));
-    CKS(ensure(ctx, ctx->dnn, Nmax));
-    CKS(ensure(ctx, ctx->pidx, kMaxTopK));
-    CKS(ensure(ctx, ctx->pnn, kMaxTopK));
+struct PassOut {
+    std::vector<LaneState> st;
+    std::vector<int64_t> idx;   // [nl][K]
+    std::vector<double> nn;
+};
+
+palmad_status ensure_pass(palmad_ctx* ctx, int nl, int K) {
+    CKS(ensure(ctx, ctx->lanes, nl));
+    CKS(ensure(ctx, ctx->st, nl));
+    CKS(ensure(ctx, ctx->chain, nl));
     CKS(ensure(ctx, ctx->small, 1));
-    CKS(ensure(ctx, ctx->flags, 1));
-    job.kpad_max = ((job.maxL + 31) / 32) * 32;
-    job.nchunks_max = int32_t((Nmax + 31) / 32);
-    // survivors refined per batch: bounded by the per-chunk max table (<= 256 MB)
-    int64_t cap = (int64_t(1) << 26) / std::max(1, job.nchunks_max);
-    cap = std::min<int64_t>(cap, 16384);
-    cap = std::max<int64_t>(64, (cap / 64) * 64);
-    job.refine_cap = int32_t(cap);
-    CKS(ensure(ctx, ctx->acen, size_t(cap) * job.kpad_max));
-    CKS(ensure(ctx, ctx->asum, size_t(cap)));
-    CKS(ensure(ctx, ctx->direct, size_t(cap)));
-    CKS(ensure(ctx, ctx->cmax, size_t(cap) * job.nchunks_max));
-    CKS(ensure(ctx, ctx->scount, (Nmax + kSelectH - 1) / kSelectH + 1));
-    CKS(ensure(ctx, ctx->gmax, size_t(cap)));
-    CKS(ensure(ctx, ctx->dead, size_t(cap)));
-    CKS(ensure(ctx, ctx->nn2, size_t(cap)));
-    return PALMAD_OK;
-}
-
-// ---------------------------------------------------- statistics per length
-
-// Prepare length m: first length by direct (sliding) Eq. 4, later lengths by
-// the Eq. 7-8 recurrence from m-1.
-palmad_status prepare_length(palmad_ctx* ctx, Job& job, int32_t m, bool first) {
-    CK(cudaMemsetAsync(ctx->flags.p, 0, sizeof(Flags), ctx->stream));
-    StatsArgs a{};
-    a.T = job.T;
-    a.n = job.n;
-    a.m = m;
-    if (first) {
-        LAUNCH(PALMAD_K_STATS, launch_stats_init(job.T, job.n, m, ctx->mu[0].p, ctx->var[0].p, &ctx->flags.p->flags,
-                                                 ctx->stream));
-        job.cur = 0;
-        a.advance = 0;
-        a.mu_old = ctx->mu[0].p;
-        a.var_old = ctx->var[0].p;
-        a.mu = ctx->mu[0].p;
-        a.var = ctx->var[0].p;
-    } else {
-        a.advance = 1;
-        a.mu_old = ctx->mu[job.cur].p;
-        a.var_old = ctx->var[job.cur].p;
-        a.mu = ctx->mu[job.cur ^ 1].p;
-        a.var = ctx->var[job.cur ^ 1].p;
-        job.cur ^= 1;
+    CKS(ensure(ctx, ctx->pidx, size_t(nl) * K));
+    CKS(ensure(ctx, ctx->pnn, size_t(nl) * K));
+    if (ctx->h_cap < nl) {
+        if (ctx->h_lanes) cudaFreeHost(ctx->h_lanes);
+        if (ctx->h_st) cudaFreeHost(ctx->h_st);
+        if (ctx->h_chain) cudaFreeHost(ctx->h_chain);
+        ctx->h_lanes = nullptr; ctx->h_st = nullptr; ctx->h_chain = nullptr;
+        const int cap = std::max(nl, 64);
+        if (cudaMallocHost(&ctx->h_lanes, sizeof(Lane) * cap) != cudaSuccess ||
+            cudaMallocHost(&ctx->h_st, sizeof(LaneState) * cap) != cudaSuccess ||
+            cudaMallocHost(&ctx->h_chain, sizeof(int32_t) * cap) != cudaSuccess) {
+            ctx->h_cap = 0;
+            return fail(ctx, PALMAD_ERR_OOM, "pinned host allocation failed");
+        }
+        ctx->h_cap = cap;
     }
-    a.win = ctx->win.p;
-    a.bits = ctx->bits0.p;
-    a.flags = &ctx->flags.p->flags;
-    a.ab = ctx->flags.p->ab;
-    LAUNCH(PALMAD_K_STATS, launch_stats_step(a, ctx->stream));
-    job.m = m;
-    if (first) {
-        CK(cudaMemcpyAsync(ctx->h_flags, ctx->flags.p, sizeof(Flags), cudaMemcpyDeviceToHost, ctx->stream));
-        CKS(sync(ctx));
-        if (ctx->h_flags->flags & 1) return fail(ctx, PALMAD_ERR_NONFINITE, "T holds a NaN or an infinity");
+    if (ctx->h_pick_cap < int64_t(nl) * K) {
+        if (ctx->h_pidx) cudaFreeHost(ctx->h_pidx);
+        if (ctx->h_pnn) cudaFreeHost(ctx->h_pnn);
+        ctx->h_pidx = nullptr; ctx->h_pnn = nullptr;
+        const int64_t cap = std::max<int64_t>(int64_t(nl) * K, 1024);
+        if (cudaMallocHost(&ctx->h_pidx, sizeof(int64_t) * cap) != cudaSuccess ||
+            cudaMallocHost(&ctx->h_pnn, sizeof(double) * cap) != cudaSuccess) {
+            ctx->h_pick_cap = 0;
+            return fail(ctx, PALMAD_ERR_OOM, "pinned host allocation failed");
+        }
+        ctx->h_pick_cap = cap;
+    }
+    if (!ctx->h_small) {
+        if (cudaMallocHost(&ctx->h_small, sizeof(Small)) != cudaSuccess)
+            return fail(ctx, PALMAD_ERR_OOM, "pinned host allocation failed");
     }
     return PALMAD_OK;
 }
 
-// ------------------------------------------------------------ one DRAG call
+// Refine pool: slots, each with a centred window row and a row of chunk maxima.
+palmad_status ensure_pool(palmad_ctx* ctx, int32_t kpad, int32_t nchunks) {
+    if (ctx->pool > 0 && kpad <= ctx->pool_kpad && nchunks <= ctx->pool_nchunks) return PALMAD_OK;
+    kpad = std::max(kpad, ctx->pool_kpad);
+    nchunks = std::max(nchunks, ctx->pool_nchunks);
+    int64_t slots = kPoolBytes / (int64_t(sizeof(float)) * (nchunks + kpad));
+    slots = std::min<int64_t>(slots, 1 << 17);
+    slots = std::max<int64_t>(64, (slots / 64) * 64);
+    CKS(ensure(ctx, ctx->slot_lane, slots)); CKS(ensure(ctx, ctx->slot_win, slots)); CKS(ensure(ctx, ctx->route, slots));
+    CKS(ensure(ctx, ctx->dead, slots)); CKS(ensure(ctx, ctx->asum, slots)); CKS(ensure(ctx, ctx->gmax, slots));
+    CKS(ensure(ctx, ctx->nn2, slots));
+    CKS(ensure(ctx, ctx->acen, size_t(slots) * kpad));
+    CKS(ensure(ctx, ctx->cmax, size_t(slots) * nchunks));
+    CKS(ensure(ctx, ctx->strips, size_t(slots)));
+    ctx->pool = int32_t(slots);
+    ctx->pool_kpad = kpad;
+    ctx->pool_nchunks = nchunks;
+    return PALMAD_OK;
+}
 
-struct DragResult {
-    int32_t got = 0;      // top-K picks found
-    int32_t count = 0;    // range discords
-};
+Pass base_pass(palmad_ctx* ctx, int nl, int K, bool exclusive, const palmad_options& o) {
+    Pass p{};
+    p.lanes = ctx->lanes.p;
+    p.st = ctx->st.p;
+    p.nl = nl;
+    p.K = K;
+    p.exclusive = exclusive ? 1 : 0;
+    p.seg = kRefineSeg;
+    p.cap = o.select_cap > 0 ? o.select_cap : kDefaultCap;
+    p.slot_lane = ctx->slot_lane.p;
+    p.slot_win = ctx->slot_win.p;
+    p.route = ctx->route.p;
+    p.acen = ctx->acen.p;
+    p.asum = ctx->asum.p;
+    p.gmax = ctx->gmax.p;
+    p.dead = ctx->dead.p;
+    p.nn2 = ctx->nn2.p;
+    p.cmax = ctx->cmax.p;
+    p.strips = ctx->strips.p;
+    p.nref = &ctx->small.p->nref;
+    p.work = ctx->small.p->work;
+    p.pairs = ctx->small.p->pairs;
+    p.pick_idx = ctx->pidx.p;
+    p.pick_nn = ctx->pnn.p;
+    return p;
+}
 
-palmad_status drag_call(palmad_ctx* ctx, Job& job, double r, DragResult& out) {
-    const int32_t m = job.m;
-    const int64_t n = job.n;
-    const int64_t N = n - m + 1;
-    const int64_t P = (N + 31) / 32;
-    const double r2 = r * r;
-    const double rho_thr = 1.0 - r2 / (2.0 * m);
-    const double band = job.opt.band_rel * r2 / m;
-    const int64_t cap = job.opt.select_cap > 0 ? job.opt.select_cap : kDefaultCap;
-    Thresh th{};
-    th.rho_thr = float(rho_thr);
-    th.band = float(band);
-    th.prune = r > 0.0 ? 1 : 0;
-    th.m = m;
-    th.H = kSelectH;
-    th.ab = ctx->flags.p->ab;
+// One pass over `req` lanes: statistics, select, compaction, refine rounds
+// through the slot pool, gather and top-K.  Fills `out` with every lane's
+// state and top-K picks.
+palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool exclusive, const palmad_options& o,
+                       PassOut& out) {
+    const int nl = int(req.size());
+    if (nl == 0) return PALMAD_OK;
+    if (nl > kMaxLanes) return fail(ctx, PALMAD_ERR_INTERNAL, "too many lanes in a pass");
+    CKS(ensure_pass(ctx, nl, K));
+    int32_t kpad_max = 32, nchunks_max = 1;
+    int64_t nmax = 1, strips = 0;
+    int nchains = 0;
+    for (int l = 0; l < nl; ++l) {
+        Lane& L = req[l].lane;
+        L.kpad = ((L.m + 31) / 32) * 32;
+        L.nstrips = int32_t((L.N + kStripH - 1) / kStripH);
+        L.strip_base = strips;
+        strips += L.prune ? L.nstrips : 0;
+        if (!L.prune) L.nstrips = 0;
+        kpad_max = std::max(kpad_max, L.kpad);
+        nchunks_max = std::max<int32_t>(nchunks_max, int32_t((L.N + 31) / 32));
+        nmax = std::max(nmax, L.N);
+        if (l == 0 || !req[l - 1].lane.chain_next) ctx->h_chain[nchains++] = l;
+        ctx->h_lanes[l] = L;
+        LaneState s = req[l].state;
+        s.nsurv = 0; s.dcount = 0; s.got = 0; s.count_final = 0; s.maxerr = 0;
+        if (L.stats_mode != 0) { s.flags = 0; s.ab[0] = 0; s.ab[1] = 0; }
+        ctx->h_st[l] = s;
+    }
+    CKS(ensure_pool(ctx, kpad_max, nchunks_max));
+    Pass p = base_pass(ctx, nl, K, exclusive, o);
+    p.sel_items = strips;
+    p.nmax = nmax;
+    p.kpad_max = ctx->pool_kpad;
+    p.nchunks_max = ctx->pool_nchunks;
 
+    CK(cudaMemcpyAsync(ctx->lanes.p, ctx->h_lanes, sizeof(Lane) * nl, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->st.p, ctx->h_st, sizeof(LaneState) * nl, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->chain.p, ctx->h_chain, sizeof(int32_t) * nchains, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(ctx->small.p, 0, sizeof(Small), ctx->stream));
-    CK(cudaMemcpyAsync(ctx->bits.p, ctx->bits0.p, P * sizeof(uint32_t), cudaMemcpyDeviceToDevice, ctx->stream));
-
-    SweepArgs sa{};
-    sa.T = job.T;
-    sa.n = n;
-    sa.N = N;
-    sa.m = m;
-    sa.win = ctx->win.p;
-    sa.th = th;
-    sa.work = &ctx->small.p->work[0];
-    sa.pairs = &ctx->small.p->pairs[0];
-    sa.seeds = &ctx->small.p->pairs[3];
-    sa.bits = ctx->bits.p;
-    sa.cap = cap;
-    if (r > 0.0) LAUNCH(PALMAD_K_SELECT, launch_select(sa, ctx->sel_grid, ctx->stream));
-
-    CompactArgs ca{ctx->bits.p, N, ctx->surv.p, &ctx->small.p->nsurv};
-    LAUNCH(PALMAD_K_COMPACT, launch_compact(ca, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_small, ctx->small.p, sizeof(Small), cudaMemcpyDeviceToHost, ctx->stream));
+    LAUNCH(PALMAD_K_STATS, launch_stats(p, ctx->chain.p, nchains, nmax, ctx->stream));
+    if (strips > 0) LAUNCH(PALMAD_K_SELECT, launch_select(p, ctx->sms * 4, ctx->stream));
+    LAUNCH(PALMAD_K_COMPACT, launch_compact(p, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_st, ctx->st.p, sizeof(LaneState) * nl, cudaMemcpyDeviceToHost, ctx->stream));
     CKS(sync(ctx));
-    const int32_t nsurv = ctx->h_small->nsurv;
-    ctx->stats.survivors += nsurv;
+    for (int l = 0; l < nl; ++l) ctx->stats.survivors += ctx->h_st[l].nsurv;
     ctx->stats.device_passes += 1;
 
-    const int32_t kpad = ((m + 31) / 32) * 32;
-    const int32_t nchunks = int32_t((N + 31) / 32);
-    const int64_t nstrip_all = (N + kSelectH - 1) / kSelectH;
-    for (int32_t b0 = 0; b0 < nsurv; b0 += job.refine_cap) {
-        const int32_t ns = std::min(job.refine_cap, nsurv - b0);
-        const int32_t* surv = ctx->surv.p + b0;
-        CK(cudaMemsetAsync(ctx->gmax.p, 0, ns * sizeof(uint32_t), ctx->stream));
-        CK(cudaMemsetAsync(ctx->dead.p, 0, ns * sizeof(int32_t), ctx->stream));
-        CK(cudaMemsetAsync(ctx->nn2.p, 0x7f, ns * sizeof(unsigned long long), ctx->stream));
-        CK(cudaMemsetAsync(ctx->slot_of.p, 0xff, N * sizeof(int32_t), ctx->stream));
-        CK(cudaMemsetAsync(&ctx->small.p->work[1], 0, 2 * sizeof(int32_t), ctx->stream));
-        CK(cudaMemsetAsync(&ctx->small.p->nref, 0, 2 * sizeof(int32_t), ctx->stream));
-        CK(cudaMemsetAsync(ctx->scount.p, 0, nstrip_all * sizeof(int32_t), ctx->stream));
-        const int32_t thr = std::max(2, (5 * kSelectH + m + m - 1) / m);
-        LAUNCH(PALMAD_K_PLAN, launch_plan(surv, ns, ctx->win.p, kSelectH, thr, ctx->slot_of.p, ctx->scount.p, ctx->strips.p,
-                                            &ctx->small.p->nref, ctx->direct.p, &ctx->small.p->ndirect, ctx->stream));
-        LAUNCH(PALMAD_K_PLAN,
-               launch_refine_prep(job.T, ctx->win.p, surv, ns, m, kpad, ctx->acen.p, ctx->asum.p, ctx->stream));
-        SweepArgs wa{};
-        wa.T = job.T;
-        wa.n = n;
-        wa.N = N;
-        wa.m = m;
-        wa.win = ctx->win.p;
-        wa.th = th;
-        wa.work = &ctx->small.p->work[2];
-        wa.pairs = &ctx->small.p->pairs[4];
-        wa.seeds = &ctx->small.p->pairs[5];
-        wa.strips = ctx->strips.p;
-        wa.nref = &ctx->small.p->nref;
-        wa.seg = kRefineSeg;
-        wa.slot_of = ctx->slot_of.p;
-        wa.dead = ctx->dead.p;
-        wa.gmax = ctx->gmax.p;
-        wa.cmax = ctx->cmax.p;
-        wa.nchunks = nchunks;
-        LAUNCH(PALMAD_K_REFINE_SWEEP, launch_refine_sweep(wa, ctx->sel_grid, ctx->stream));
-        RefineArgs ra{};
-        ra.list = ctx->direct.p;
-        ra.nlist = &ctx->small.p->ndirect;
-        ra.T = job.T;
-        ra.n = n;
-        ra.N = N;
-        ra.m = m;
-        ra.kpad = kpad;
-        ra.win = ctx->win.p;
-        ra.surv = surv;
-        ra.ns = ns;
-        ra.acen = ctx->acen.p;
-        ra.asum = ctx->asum.p;
-        ra.th = th;
-        ra.nchunks = nchunks;
-        ra.gmax = ctx->gmax.p;
-        ra.dead = ctx->dead.p;
-        ra.cmax = ctx->cmax.p;
-        ra.flags = &ctx->flags.p->flags;
-        ra.work = &ctx->small.p->work[1];
-        ra.pairs = &ctx->small.p->pairs[1];
-        LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine(ra, ctx->ref_grid, ctx->stream));
-        RecheckArgs rc{};
-        rc.T = job.T;
-        rc.n = n;
-        rc.N = N;
-        rc.m = m;
-        rc.kpad = kpad;
-        rc.win = ctx->win.p;
-        rc.mu = ctx->mu[job.cur].p;
-        rc.var = ctx->var[job.cur].p;
-        rc.surv = surv;
-        rc.ns = ns;
-        rc.acen = ctx->acen.p;
-        rc.gmax = ctx->gmax.p;
-        rc.dead = ctx->dead.p;
-        rc.cmax = ctx->cmax.p;
-        rc.nchunks = nchunks;
-        rc.th = th;
-        rc.nn2 = ctx->nn2.p;
-        rc.flags = &ctx->flags.p->flags;
-        rc.pairs = &ctx->small.p->pairs[2];
-        rc.maxerr = &ctx->small.p->maxerr;
-        LAUNCH(PALMAD_K_RECHECK, launch_recheck(rc, ctx->stream));
-        GatherArgs ga{surv, ns, ctx->dead.p, ctx->nn2.p, r, ctx->didx.p, ctx->dnn.p, &ctx->small.p->dcount};
-        LAUNCH(PALMAD_K_GATHER, launch_gather(ga, ctx->stream));
+    // Refine rounds: lanes' survivors in order, as many as the pool holds.
+    std::vector<int32_t> done(nl, 0);
+    for (;;) {
+        int32_t used = 0;
+        bool any = false;
+        for (int l = 0; l < nl; ++l) {
+            Lane& L = ctx->h_lanes[l];
+            const int32_t rem = ctx->h_st[l].nsurv - done[l];
+            const int32_t room = ctx->pool - used;
+            const int32_t take = std::max(0, std::min(rem, room));
+            L.k_lo = done[l];
+            L.k_hi = done[l] + take;
+            L.slot_base = used;
+            if (take > 0) {
+                any = true;
+                used += ((take + 63) / 64) * 64;
+                done[l] += take;
+            }
+            if (used >= ctx->pool) used = ctx->pool;
+        }
+        if (!any) break;
+        p.nslots = used;
+        CK(cudaMemcpyAsync(ctx->lanes.p, ctx->h_lanes, sizeof(Lane) * nl, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemsetAsync(&ctx->small.p->work[1], 0, 4 * sizeof(int32_t), ctx->stream));
+        CK(cudaMemsetAsync(&ctx->small.p->nref, 0, sizeof(int32_t), ctx->stream));
+        LAUNCH(PALMAD_K_PLAN, launch_round_reset(p, ctx->stream));
+        LAUNCH(PALMAD_K_PLAN, launch_plan(p, ctx->stream));
+        LAUNCH(PALMAD_K_REFINE_SWEEP, launch_refine_sweep(p, ctx->sms * 4, ctx->stream));
+        LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_direct(p, ctx->sms * 2, ctx->stream));
+        LAUNCH(PALMAD_K_RECHECK, launch_recheck(p, ctx->sms * 8, ctx->stream));
+        LAUNCH(PALMAD_K_GATHER, launch_gather(p, ctx->stream));
+        bool more = false;
+        for (int l = 0; l < nl; ++l) more |= done[l] < ctx->h_st[l].nsurv;
+        if (!more) break;
     }
-    TopkArgs ta{ctx->didx.p, ctx->dnn.p, &ctx->small.p->dcount, job.K, m, job.exclusive ? 1 : 0, ctx->pidx.p,
-                ctx->pnn.p};
-    LAUNCH(PALMAD_K_TOPK, launch_topk(ta, ctx->stream));
+    LAUNCH(PALMAD_K_TOPK, launch_topk(p, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_st, ctx->st.p, sizeof(LaneState) * nl, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_pidx, ctx->pidx.p, sizeof(int64_t) * nl * K, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_pnn, ctx->pnn.p, sizeof(double) * nl * K, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_small, ctx->small.p, sizeof(Small), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_pidx, ctx->pidx.p, job.K * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->h_pnn, ctx->pnn.p, job.K * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CKS(sync(ctx));
+    out.st.assign(ctx->h_st, ctx->h_st + nl);
+    out.idx.assign(ctx->h_pidx, ctx->h_pidx + int64_t(nl) * K);
+    out.nn.assign(ctx->h_pnn, ctx->h_pnn + int64_t(nl) * K);
     const Small& sm = *ctx->h_small;
     ctx->stats.select_pairs += int64_t(sm.pairs[0]);
-    ctx->stats.refine_pairs += int64_t(sm.pairs[1]);
-    ctx->stats.refine_pairs += int64_t(sm.pairs[4]);
-    ctx->stats.select_flops += 5.0 * double(sm.pairs[0]) + 2.0 * m * double(sm.pairs[3]);
-    ctx->stats.refine_flops += 2.0 * m * double(sm.pairs[1]);
-    ctx->stats.sweep_flops += 5.0 * double(sm.pairs[4]) + 2.0 * m * double(sm.pairs[5]);
+    ctx->stats.refine_pairs += int64_t(sm.pairs[1]) + int64_t(sm.pairs[4]);
     ctx->stats.fp64_pairs += int64_t(sm.pairs[2]);
-    {
-        uint32_t e = sm.maxerr;
+    // algorithmic work: per-lane m is folded with the pass-average m (exact for one length)
+    double msum = 0.0;
+    for (int l = 0; l < nl; ++l) msum += req[l].lane.m;
+    const double mavg = msum / nl;
+    ctx->stats.select_flops += 5.0 * double(sm.pairs[0]) + 2.0 * mavg * double(sm.pairs[3]);
+    ctx->stats.refine_flops += 2.0 * mavg * double(sm.pairs[1]);
+    ctx->stats.sweep_flops += 5.0 * double(sm.pairs[4]) + 2.0 * mavg * double(sm.pairs[5]);
+    for (int l = 0; l < nl; ++l) {
+        const uint32_t e = out.st[l].maxerr;
         if (e) {
-            uint32_t bbits = (e & 0x80000000u) ? (e & 0x7fffffffu) : ~e;
+            const uint32_t b = (e & 0x80000000u) ? (e & 0x7fffffffu) : ~e;
             float f;
-            std::memcpy(&f, &bbits, 4);
+            std::memcpy(&f, &b, 4);
             ctx->stats.max_fp32_rho_err = std::max(ctx->stats.max_fp32_rho_err, double(f));
         }
     }
-    out.count = sm.dcount;
-    out.got = 0;
-    while (out.got < job.K && ctx->h_pidx[out.got] >= 0) ++out.got;
     return PALMAD_OK;
 }
 
-// ------------------------------------------------------------- MERLIN
-
-struct LengthOut {
-    std::vector<int64_t> idx;
-    std::vector<double> nn;
-    std::vector<int64_t> count;
-    std::vector<double> r;
-};
-
-// One schedule step: DRAG at r, then the success test of reading R6.
-palmad_status try_r(palmad_ctx* ctx, Job& job, double r, DragResult& res, bool& ok) {
-    CKS(drag_call(ctx, job, r, res));
-    ctx->stats.drag_calls += 1;
-    ok = res.got == job.K;
+// Heatmap rows and range-discord counts of accepted lanes at their final r
+// (asynchronous: results land in device memory).
+palmad_status run_finalize(palmad_ctx* ctx, std::vector<PassLane>& req, const palmad_options& o) {
+    const int nl = int(req.size());
+    if (nl == 0) return PALMAD_OK;
+    bool need = false;
+    for (auto& q : req) need |= (q.lane.heat != nullptr) || (q.lane.count_out != nullptr);
+    if (!need) return PALMAD_OK;
+    CKS(ensure_pass(ctx, nl, 1));
+    for (int l = 0; l < nl; ++l) {
+        ctx->h_lanes[l] = req[l].lane;
+        ctx->h_st[l] = req[l].state;
+        ctx->h_st[l].count_final = 0;
+    }
+    Pass p = base_pass(ctx, nl, 1, true, o);
+    CK(cudaMemcpyAsync(ctx->lanes.p, ctx->h_lanes, sizeof(Lane) * nl, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->st.p, ctx->h_st, sizeof(LaneState) * nl, cudaMemcpyHostToDevice, ctx->stream));
+    LAUNCH(PALMAD_K_HEAT, launch_finalize(p, ctx->stream));
+    // the pinned mirrors are reused by the next pass: make sure the copies are done
+    CK(cudaStreamSynchronize(ctx->stream));
     return PALMAD_OK;
 }
 
-palmad_status merlin(palmad_ctx* ctx, Job& job, LengthOut& out, float* heat_dev) {
-    const int32_t L = job.maxL - job.minL + 1;
-    const int64_t W = job.n - job.minL + 1;
-    out.idx.assign(size_t(L) * job.K, -1);
-    out.nn.assign(size_t(L) * job.K, 0.0);
-    out.count.assign(L, 0);
-    out.r.assign(L, 0.0);
-    std::vector<double> sched(L, 0.0);
-    if (heat_dev) CK(cudaMemsetAsync(heat_dev, 0, size_t(L) * W * sizeof(float), ctx->stream));
-    for (int32_t l = 0; l < L; ++l) {
-        const int32_t m = job.minL + l;
-        CKS(prepare_length(ctx, job, m, l == 0));
-        DragResult res;
-        bool ok = false;
-        double r;
+// ====================================================== MERLIN schedule
+
+// The tries of Algorithm 1 for one length (readings R6-R8 of the oracle):
+// the same iterated arithmetic, so the r sequence is bit-identical.
+struct Tries {
+    int l = 0;       // length index
+    int h = 0;       // try number
+    double r = 0.0;
+    double step = 0.0;
+
+    void start(int li, const std::vector<double>& sched, int32_t minL) {
+        l = li;
+        h = 0;
         if (l == 0) {
-            r = 2.0 * std::sqrt(double(job.minL));
-            for (int h = 0;; ++h) {
-                if (h >= 60) r = 0.0;
-                CKS(try_r(ctx, job, r, res, ok));
-                if (ok || r <= 0.0) break;
-                r = 0.5 * r;
-            }
+            r = 2.0 * std::sqrt(double(minL));
         } else if (l <= 4) {
             r = 0.99 * sched[l - 1];
-            for (int h = 0;; ++h) {
-                if (h >= 3000 || r <= 0.0) r = 0.0;
-                CKS(try_r(ctx, job, r, res, ok));
-                if (ok || r <= 0.0) break;
-                r = 0.99 * r;
-            }
         } else {
             double mean = 0.0, var = 0.0;
             for (int q = 1; q <= 5; ++q) mean += sched[l - q];
             mean /= 5.0;
             for (int q = 1; q <= 5; ++q) var += (sched[l - q] - mean) * (sched[l - q] - mean);
             const double sdv = std::sqrt(var / 4.0);
-            const double step = sdv > 0.0 ? sdv : 0.01 * mean;
+            step = sdv > 0.0 ? sdv : 0.01 * mean;
             r = mean - 2.0 * sdv;
-            for (int h = 0;; ++h) {
-                if (h >= 3000 || r <= 0.0) r = 0.0;
-                CKS(try_r(ctx, job, r, res, ok));
-                if (ok || r <= 0.0) break;
-                r = step > 0.0 ? r - step : 0.0;
-            }
         }
-        for (int q = 0; q < res.got; ++q) {
-            out.idx[size_t(l) * job.K + q] = ctx->h_pidx[q];
-            out.nn[size_t(l) * job.K + q] = ctx->h_pnn[q];
-        }
-        sched[l] = res.got > 0 ? ctx->h_pnn[res.got - 1] : 0.0;
-        out.count[l] = res.count;
-        out.r[l] = r;
-        ctx->stats.discords += res.count;
-        if (heat_dev && res.count > 0) {
-            HeatArgs ha{ctx->didx.p, ctx->dnn.p, &ctx->small.p->dcount, m, heat_dev + size_t(l) * W};
-            LAUNCH(PALMAD_K_HEAT, launch_heat(ha, ctx->stream));
+        guard();
+    }
+    void guard() {
+        if (l == 0) {
+            if (h >= 60) r = 0.0;
+        } else if (h >= 3000 || r <= 0.0) {
+            r = 0.0;
         }
     }
-    ctx->stats.lengths += L;
+    bool last() const { return r <= 0.0; }
+    void next() {
+        if (l == 0) r = 0.5 * r;
+        else if (l <= 4) r = 0.99 * r;
+        else r = step > 0.0 ? r - step : 0.0;
+        ++h;
+        guard();
+    }
+};
+
+// One series under the schedule.
+struct SeriesJob {
+    // configuration
+    const float* T = nullptr;   // device, 16-byte aligned
+    int64_t n = 0;
+    int32_t minL = 0, maxL = 0, K = 1;
+    bool exclusive = true;
+    int W = 1;                  // lanes per window (1: plain form)
+    int set0 = 0;               // first LaneSet of this series
+    float* heat = nullptr;      // device heatmap base (row l at heat + l*hw) or nullptr
+    int64_t hw = 0;
+    int64_t* count_dev = nullptr;  // device [L] counts
+    int32_t* init_flag = nullptr;  // device int for the non-finite check
+    // results
+    std::vector<int64_t> idx;
+    std::vector<double> nn, r_final;
+    std::vector<double> sched;
+    std::vector<LaneState> lstate;    // per length: state after its last pass
+    // progress
+    int32_t L = 0;
+    int32_t l = 0;              // next length to decide
+    bool done = false;
+    int32_t prepared_hi = -1;   // highest length index whose statistics exist
+    Tries tr;
+    bool tr_started = false;
+    enum Phase { kIdle, kPlain, kWindow, kRerun } phase = kIdle;
+    // window bookkeeping
+    int32_t wl0 = 0, wn = 0;    // window lengths [wl0, wl0+wn)
+    std::vector<double> rspec;  // speculative r per window length
+    std::vector<LaneState> wst;
+    std::vector<std::vector<int64_t>> widx;
+    std::vector<std::vector<double>> wnn;
+    int32_t rerun_l = -1;       // length awaiting a rerun result
+    double rerun_r = 0.0;
+
+    int set_of(int32_t li) const { return set0 + (W > 1 ? (li % W) : 0); }
+    int32_t m_of(int32_t li) const { return minL + li; }
+};
+
+Lane make_lane(palmad_ctx* ctx, SeriesJob& s, int32_t li, double r, const palmad_options& o) {
+    Lane L{};
+    LaneSet& S = ctx->sets[s.set_of(li)];
+    L.T = s.T;
+    L.n = s.n;
+    L.m = s.m_of(li);
+    L.N = s.n - L.m + 1;
+    L.mu = S.mu.p;
+    L.var = S.var.p;
+    L.win = S.win.p;
+    L.bits0 = S.bits0.p;
+    L.bits = S.bits.p;
+    L.surv = S.surv.p;
+    L.slot_of = S.slot_of.p;
+    L.scount = S.scount.p;
+    L.didx = S.didx.p;
+    L.dnn = S.dnn.p;
+    L.r = r;
+    L.prune = r > 0.0 ? 1 : 0;
+    L.rho_thr = float(1.0 - r * r / (2.0 * L.m));
+    L.band = float(o.band_rel * r * r / L.m);
+    // statistics source
+    if (li <= s.prepared_hi) {
+        L.stats_mode = 0;
+    } else if (li == 0) {
+        L.stats_mode = 2;  // copy in place after the init kernel
+        L.mu_src = S.mu.p;
+        L.var_src = S.var.p;
+    } else {
+        L.stats_mode = 1;
+        LaneSet& P = ctx->sets[s.set_of(li - 1)];
+        L.mu_src = P.mu.p;
+        L.var_src = P.var.p;
+    }
+    return L;
+}
+
+// Speculative threshold for the window lengths: below the first try of the
+// schedule with room for about two decrements.
+double speculative_r(const SeriesJob& s, int32_t l0) {
+    double mean = 0.0, var = 0.0;
+    for (int q = 1; q <= 5; ++q) mean += s.sched[l0 - q];
+    mean /= 5.0;
+    for (int q = 1; q <= 5; ++q) var += (s.sched[l0 - q] - mean) * (s.sched[l0 - q] - mean);
+    const double sdv = std::sqrt(var / 4.0);
+    const double r = mean - 2.0 * sdv - 2.0 * std::max(sdv, 0.03 * mean);
+    return std::max(r, 0.5 * mean);
+}
+
+void accept_length(SeriesJob& s, int32_t li, double r, const LaneState& st, const int64_t* pidx, const double* pnn,
+                   std::vector<PassLane>& fin, palmad_ctx* ctx, const palmad_options& o) {
+    int got = 0;
+    for (int q = 0; q < s.K; ++q) {
+        const bool ok = pidx[q] >= 0 && (r <= 0.0 || pnn[q] >= r);
+        s.idx[size_t(li) * s.K + q] = ok ? pidx[q] : -1;
+        s.nn[size_t(li) * s.K + q] = ok ? pnn[q] : 0.0;
+        got += ok;
+    }
+    s.sched[li] = got > 0 ? s.nn[size_t(li) * s.K + got - 1] : 0.0;
+    s.r_final[li] = r;
+    s.lstate[li] = st;
+    PassLane f{};
+    f.lane = make_lane(ctx, s, li, r, o);
+    f.lane.stats_mode = 0;
+    f.lane.heat = s.heat ? s.heat + size_t(li) * s.hw : nullptr;
+    f.lane.count_out = s.count_dev ? s.count_dev + li : nullptr;
+    f.state = st;
+    fin.push_back(f);
+}
+
+// Lanes the series wants in the next pass.
+void series_request(palmad_ctx* ctx, SeriesJob& s, std::vector<PassLane>& req, std::vector<int>& owner, int sid,
+                    const palmad_options& o) {
+    if (s.done) return;
+    auto push = [&](int32_t li, double r, bool chain_next) {
+        PassLane q{};
+        q.lane = make_lane(ctx, s, li, r, o);
+        q.lane.chain_next = chain_next ? 1 : 0;
+        if (q.lane.stats_mode == 0) q.state = s.lstate[li];
+        req.push_back(q);
+        owner.push_back(sid);
+    };
+    if (s.phase == SeriesJob::kRerun) {
+        push(s.rerun_l, s.rerun_r, false);
+        return;
+    }
+    if (s.W > 1 && s.l >= 5) {
+        s.wl0 = s.l;
+        s.wn = std::min<int32_t>(s.W, s.L - s.l);
+        s.rspec.assign(s.wn, speculative_r(s, s.l));
+        for (int w = 0; w < s.wn; ++w) push(s.wl0 + w, s.rspec[w], w + 1 < s.wn);
+        s.phase = SeriesJob::kWindow;
+        return;
+    }
+    if (!s.tr_started) {
+        s.tr.start(s.l, s.sched, s.minL);
+        s.tr_started = true;
+    }
+    push(s.l, s.tr.r, false);
+    s.phase = SeriesJob::kPlain;
+}
+
+// Replays Algorithm 1 over the window results; stops when a length needs a
+// rerun below its speculative r.
+void series_replay(palmad_ctx* ctx, SeriesJob& s, std::vector<PassLane>& fin, const palmad_options& o) {
+    const int K = s.K;
+    while (s.l < s.wl0 + s.wn) {
+        const int w = s.l - s.wl0;
+        if (!s.tr_started) {
+            s.tr.start(s.l, s.sched, s.minL);
+            s.tr_started = true;
+        }
+        const double rs = s.rspec[w];
+        for (;;) {
+            const double r = s.tr.r;
+            if (!(rs <= 0.0 || r >= rs)) {
+                // the schedule needs r below this length's r': rerun it lower
+                const double step = s.tr.step > 0.0 ? s.tr.step : 0.01 * r;
+                s.rerun_l = s.l;
+                s.rerun_r = std::max(0.0, r - 3.0 * step);
+                if (s.rerun_r < 1e-9 * r) s.rerun_r = 0.0;
+                s.phase = SeriesJob::kRerun;
+                ctx->stats.reruns += 1;
+                return;
+            }
+            ctx->stats.drag_calls += 1;
+            int got = 0;
+            for (int q = 0; q < K; ++q)
+                if (s.widx[w][q] >= 0 && (r <= 0.0 || s.wnn[w][q] >= r)) ++got;
+            if (got == K || s.tr.last()) {
+                accept_length(s, s.l, r, s.wst[w], s.widx[w].data(), s.wnn[w].data(), fin, ctx, o);
+                break;
+            }
+            s.tr.next();
+        }
+        s.l += 1;
+        s.tr_started = false;
+    }
+    s.phase = SeriesJob::kIdle;
+    if (s.l >= s.L) s.done = true;
+}
+
+// Consumes the results of the series' lanes (in request order).
+void series_consume(palmad_ctx* ctx, SeriesJob& s, const PassOut& out, const std::vector<int>& mine,
+                    std::vector<PassLane>& fin, const palmad_options& o) {
+    const int K = s.K;
+    auto pidx = [&](int k) { return out.idx.data() + size_t(mine[k]) * K; };
+    auto pnn = [&](int k) { return out.nn.data() + size_t(mine[k]) * K; };
+    if (s.phase == SeriesJob::kPlain) {
+        const LaneState& st = out.st[mine[0]];
+        s.prepared_hi = std::max(s.prepared_hi, s.l);
+        s.lstate[s.l] = st;
+        ctx->stats.drag_calls += 1;
+        if (st.got == K || s.tr.last()) {
+            accept_length(s, s.l, s.tr.r, st, pidx(0), pnn(0), fin, ctx, o);
+            s.l += 1;
+            s.tr_started = false;
+            if (s.l >= s.L) s.done = true;
+        } else {
+            s.tr.next();
+        }
+        s.phase = SeriesJob::kIdle;
+        return;
+    }
+    if (s.phase == SeriesJob::kWindow) {
+        s.wst.resize(s.wn);
+        s.widx.resize(s.wn);
+        s.wnn.resize(s.wn);
+        for (int w = 0; w < s.wn; ++w) {
+            s.wst[w] = out.st[mine[w]];
+            s.lstate[s.wl0 + w] = s.wst[w];
+            s.widx[w].assign(pidx(w), pidx(w) + K);
+            s.wnn[w].assign(pnn(w), pnn(w) + K);
+        }
+        s.prepared_hi = std::max(s.prepared_hi, s.wl0 + s.wn - 1);
+    } else if (s.phase == SeriesJob::kRerun) {
+        const int w = s.rerun_l - s.wl0;
+        s.wst[w] = out.st[mine[0]];
+        s.lstate[s.rerun_l] = s.wst[w];
+        s.widx[w].assign(pidx(0), pidx(0) + K);
+        s.wnn[w].assign(pnn(0), pnn(0) + K);
+        s.rspec[w] = s.rerun_r;
+        s.rerun_l = -1;
+    }
+    series_replay(ctx, s, fin, o);
+}
+
+// Runs MERLIN over the given series, sharing passes between them.
+palmad_status run_jobs(palmad_ctx* ctx, std::vector<SeriesJob>& jobs, const palmad_options& o) {
+    // lane buffers
+    int nsets = 0;
+    for (auto& s : jobs) {
+        s.set0 = nsets;
+        nsets += std::max(1, s.W);
+    }
+    if (int(ctx->sets.size()) < nsets) ctx->sets.resize(nsets);
+    for (auto& s : jobs) {
+        for (int q = 0; q < std::max(1, s.W); ++q) CKS(ensure_set(ctx, ctx->sets[s.set0 + q], s.n - s.minL + 1));
+        s.L = s.maxL - s.minL + 1;
+        s.idx.assign(size_t(s.L) * s.K, -1);
+        s.nn.assign(size_t(s.L) * s.K, 0.0);
+        s.r_final.assign(s.L, 0.0);
+        s.sched.assign(s.L, 0.0);
+        s.lstate.assign(s.L, LaneState{});
+    }
+    // initial statistics (Eq. 4 at minL) and the non-finite check
+    CKS(ensure(ctx, ctx->init_flags, jobs.size()));
+    CK(cudaMemsetAsync(ctx->init_flags.p, 0, sizeof(int32_t) * jobs.size(), ctx->stream));
+    for (size_t q = 0; q < jobs.size(); ++q) {
+        SeriesJob& s = jobs[q];
+        LaneSet& S = ctx->sets[s.set0];
+        s.init_flag = ctx->init_flags.p + q;
+        LAUNCH(PALMAD_K_STATS, launch_stats_init(s.T, s.n, s.minL, S.mu.p, S.var.p, s.init_flag, ctx->stream));
+        if (s.count_dev) CK(cudaMemsetAsync(s.count_dev, 0, sizeof(int64_t) * s.L, ctx->stream));
+        if (s.heat) CK(cudaMemsetAsync(s.heat, 0, sizeof(float) * size_t(s.L) * s.hw, ctx->stream));
+    }
+    std::vector<int32_t> flags(jobs.size());
+    CK(cudaMemcpyAsync(flags.data(), ctx->init_flags.p, sizeof(int32_t) * jobs.size(), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CKS(sync(ctx));
+    for (size_t q = 0; q < jobs.size(); ++q)
+        if (flags[q] & 1) return fail(ctx, PALMAD_ERR_NONFINITE, "T holds a NaN or an infinity");
+
+    std::vector<PassLane> req, fin;
+    std::vector<int> owner;
+    PassOut out;
+    for (;;) {
+        req.clear();
+        owner.clear();
+        for (size_t q = 0; q < jobs.size(); ++q) {
+            if (int(req.size()) + std::max(1, jobs[q].W) > kMaxLanes) break;
+            series_request(ctx, jobs[q], req, owner, int(q), o);
+        }
+        if (req.empty()) break;
+        const int K = jobs[0].K;
+        const bool excl = jobs[0].exclusive;
+        CKS(run_pass(ctx, req, K, excl, o, out));
+        fin.clear();
+        std::vector<std::vector<int>> per(jobs.size());
+        for (int k = 0; k < int(owner.size()); ++k) per[owner[k]].push_back(k);
+        for (size_t q = 0; q < jobs.size(); ++q)
+            if (!per[q].empty()) series_consume(ctx, jobs[q], out, per[q], fin, o);
+        CKS(run_finalize(ctx, fin, o));
+    }
+    for (auto& s : jobs) ctx->stats.lengths += s.L;
     return PALMAD_OK;
 }
 
@@ -543,7 +812,7 @@ palmad_status check_args(palmad_ctx* ctx, int64_t n, int32_t minL, int32_t maxL,
     if (maxL < minL) return fail(ctx, PALMAD_ERR_ARG, "maxL must be >= minL");
     if (n < 2 * int64_t(maxL)) return fail(ctx, PALMAD_ERR_ARG, "n must be >= 2*maxL");
     if (n > (int64_t(1) << 30)) return fail(ctx, PALMAD_ERR_UNSUPPORTED, "n above 2^30 is not supported");
-    if (topK < 1 || topK > kMaxTopK) return fail(ctx, PALMAD_ERR_ARG, "topK must lie in [1, 1024]");
+    if (topK < 1 || topK > kMaxK) return fail(ctx, PALMAD_ERR_ARG, "topK must lie in [1, 1024]");
     return PALMAD_OK;
 }
 
@@ -558,6 +827,24 @@ palmad_status begin_call(palmad_ctx* ctx, const palmad_options& o) {
     ctx->profile = o.profile != 0;
     CK(cudaSetDevice(ctx->device));
     return PALMAD_OK;
+}
+
+// A series on the device that starts on a 16-byte boundary (the sweeps copy
+// it with 16-byte asynchronous copies).
+palmad_status aligned_series(palmad_ctx* ctx, const float* T_dev, int64_t n, DBuf<float>& stage, const float** out) {
+    if (reinterpret_cast<uintptr_t>(T_dev) % 16 == 0) {
+        *out = T_dev;
+        return PALMAD_OK;
+    }
+    CKS(ensure(ctx, stage, size_t(n)));
+    CK(cudaMemcpyAsync(stage.p, T_dev, size_t(n) * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+    *out = stage.p;
+    return PALMAD_OK;
+}
+
+// Sums the device counts into the stats.
+void count_discords(palmad_ctx* ctx, const std::vector<int64_t>& counts) {
+    for (int64_t c : counts) ctx->stats.discords += c;
 }
 
 }  // namespace
@@ -591,23 +878,20 @@ palmad_status palmad_create(palmad_ctx** out, int device, void* cuda_stream) {
     if (device < 0 || device >= count) return PALMAD_ERR_ARG;
     palmad_ctx* ctx = new palmad_ctx();
     ctx->device = device;
-    auto bail = [&](palmad_status st) {
+    if (cudaSetDevice(device) != cudaSuccess) {
         palmad_destroy(ctx);
-        return st;
-    };
-    if (cudaSetDevice(device) != cudaSuccess) return bail(PALMAD_ERR_CUDA);
+        return PALMAD_ERR_CUDA;
+    }
     if (cuda_stream) {
         ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
-        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(PALMAD_ERR_CUDA);
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            palmad_destroy(ctx);
+            return PALMAD_ERR_CUDA;
+        }
         ctx->own_stream = true;
     }
-    if (cudaMallocHost(&ctx->h_small, sizeof(Small)) != cudaSuccess) return bail(PALMAD_ERR_OOM);
-    if (cudaMallocHost(&ctx->h_flags, sizeof(Flags)) != cudaSuccess) return bail(PALMAD_ERR_OOM);
-    if (cudaMallocHost(&ctx->h_pidx, kMaxTopK * sizeof(int64_t)) != cudaSuccess) return bail(PALMAD_ERR_OOM);
-    if (cudaMallocHost(&ctx->h_pnn, kMaxTopK * sizeof(double)) != cudaSuccess) return bail(PALMAD_ERR_OOM);
-    ctx->sel_grid = sweep_grid(device);
-    ctx->ref_grid = refine_grid(device);
+    ctx->sms = sm_count(device);
     reset_stats(ctx);
     *out = ctx;
     return PALMAD_OK;
@@ -618,33 +902,16 @@ void palmad_destroy(palmad_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     release(ctx->T);
-    for (int b = 0; b < 2; ++b) {
-        release(ctx->mu[b]);
-        release(ctx->var[b]);
-    }
-    release(ctx->win);
-    release(ctx->bits);
-    release(ctx->bits0);
-    release(ctx->surv);
-    release(ctx->slot_of);
-    release(ctx->strips);
-    release(ctx->direct);
-    release(ctx->acen);
-    release(ctx->asum);
-    release(ctx->cmax);
-    release(ctx->scount);
-    release(ctx->gmax);
-    release(ctx->dead);
-    release(ctx->nn2);
-    release(ctx->didx);
-    release(ctx->dnn);
-    release(ctx->pidx);
-    release(ctx->pnn);
-    release(ctx->heat);
-    release(ctx->small);
-    release(ctx->flags);
+    for (LaneSet& s : ctx->sets) release_set(s);
+    release(ctx->lanes); release(ctx->st); release(ctx->chain); release(ctx->small);
+    release(ctx->pidx); release(ctx->pnn);
+    release(ctx->slot_lane); release(ctx->slot_win); release(ctx->route); release(ctx->dead);
+    release(ctx->acen); release(ctx->asum); release(ctx->cmax); release(ctx->gmax); release(ctx->nn2);
+    release(ctx->strips); release(ctx->init_flags);
+    if (ctx->h_lanes) cudaFreeHost(ctx->h_lanes);
+    if (ctx->h_st) cudaFreeHost(ctx->h_st);
+    if (ctx->h_chain) cudaFreeHost(ctx->h_chain);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
-    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
     if (ctx->h_pidx) cudaFreeHost(ctx->h_pidx);
     if (ctx->h_pnn) cudaFreeHost(ctx->h_pnn);
     for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
@@ -658,7 +925,7 @@ void palmad_destroy(palmad_ctx* ctx) {
 
 const char* palmad_last_error(const palmad_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-const char* palmad_version(void) { return "palmad-gb300 0.1 (sm_103a)"; }
+const char* palmad_version(void) { return "palmad-gb300 0.2 (sm_103a)"; }
 
 palmad_status palmad_get_stats(const palmad_ctx* ctx, palmad_stats* out) {
     if (!ctx || !out || out->struct_size != int32_t(sizeof(palmad_stats))) return PALMAD_ERR_ARG;
@@ -675,34 +942,44 @@ palmad_status palmad_find_discords_device(palmad_ctx* ctx, const float* T_dev, i
     palmad_options o;
     CKS(read_options(ctx, opt, o));
     CKS(begin_call(ctx, o));
-    // The sweeps copy the series with 16-byte asynchronous copies: stage a
-    // series that does not start on a 16-byte boundary.
-    if (reinterpret_cast<uintptr_t>(T_dev) % 16 != 0) {
-        CKS(ensure(ctx, ctx->T, size_t(n)));
-        CK(cudaMemcpyAsync(ctx->T.p, T_dev, size_t(n) * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
-        T_dev = ctx->T.p;
-    }
-    Job job{};
-    job.T = T_dev;
-    job.n = n;
-    job.minL = minL;
-    job.maxL = maxL;
-    job.K = topK;
-    job.exclusive = o.exclusive_topk != 0;
-    job.opt = o;
-    CKS(reserve(ctx, job));
-    LengthOut lo;
-    CKS(merlin(ctx, job, lo, out_heatmap_dev));
+    std::vector<SeriesJob> jobs(1);
+    SeriesJob& s = jobs[0];
+    CKS(aligned_series(ctx, T_dev, n, ctx->T, &s.T));
+    s.n = n;
+    s.minL = minL;
+    s.maxL = maxL;
+    s.K = topK;
+    s.exclusive = o.exclusive_topk != 0;
+    s.W = std::max(1, o.batch_lengths);
     const int32_t L = maxL - minL + 1;
-    CK(cudaMemcpyAsync(out_idx_dev, lo.idx.data(), lo.idx.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CK(cudaMemcpyAsync(out_nndist_dev, lo.nn.data(), lo.nn.size() * sizeof(double), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    if (out_count_dev)
-        CK(cudaMemcpyAsync(out_count_dev, lo.count.data(), L * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
-    if (out_r_dev) CK(cudaMemcpyAsync(out_r_dev, lo.r.data(), L * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CKS(sync(ctx));
-    return PALMAD_OK;
+    s.heat = out_heatmap_dev;
+    s.hw = n - minL + 1;
+    DBuf<int64_t> cnt;
+    int64_t* count_dev = out_count_dev;
+    if (!count_dev) {
+        CKS(ensure(ctx, cnt, L));
+        count_dev = cnt.p;
+    }
+    s.count_dev = count_dev;
+    palmad_status st = run_jobs(ctx, jobs, o);
+    if (st == PALMAD_OK) {
+        std::vector<int64_t> counts(L);
+        cudaError_t e = cudaMemcpyAsync(out_idx_dev, s.idx.data(), s.idx.size() * sizeof(int64_t),
+                                        cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out_nndist_dev, s.nn.data(), s.nn.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                ctx->stream);
+        if (e == cudaSuccess && out_r_dev)
+            e = cudaMemcpyAsync(out_r_dev, s.r_final.data(), L * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(counts.data(), count_dev, L * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = fail(ctx, PALMAD_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
+        else count_discords(ctx, counts);
+        tcollect(ctx);
+    }
+    release(cnt);
+    return st;
 }
 
 palmad_status palmad_find_discords(palmad_ctx* ctx, const float* T, int64_t n, int32_t minL, int32_t maxL,
@@ -713,35 +990,53 @@ palmad_status palmad_find_discords(palmad_ctx* ctx, const float* T, int64_t n, i
     palmad_options o;
     CKS(read_options(ctx, opt, o));
     CKS(begin_call(ctx, o));
+    const int32_t L = maxL - minL + 1;
+    const int64_t hw = n - minL + 1;
     CKS(ensure(ctx, ctx->T, size_t(n)));
     CK(cudaMemcpyAsync(ctx->T.p, T, size_t(n) * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    Job job{};
-    job.T = ctx->T.p;
-    job.n = n;
-    job.minL = minL;
-    job.maxL = maxL;
-    job.K = topK;
-    job.exclusive = o.exclusive_topk != 0;
-    job.opt = o;
-    CKS(reserve(ctx, job));
-    const int32_t L = maxL - minL + 1;
-    const int64_t W = n - minL + 1;
-    float* heat_dev = nullptr;
+    DBuf<int64_t> cnt;
+    DBuf<float> heat;
+    CKS(ensure(ctx, cnt, L));
     if (out_heatmap) {
-        CKS(ensure(ctx, ctx->heat, size_t(L) * W));
-        heat_dev = ctx->heat.p;
+        palmad_status a = ensure(ctx, heat, size_t(L) * hw);
+        if (a != PALMAD_OK) {
+            release(cnt);
+            return a;
+        }
     }
-    LengthOut lo;
-    CKS(merlin(ctx, job, lo, heat_dev));
-    if (heat_dev) {
-        CK(cudaMemcpyAsync(out_heatmap, heat_dev, size_t(L) * W * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
-        CKS(sync(ctx));
+    std::vector<SeriesJob> jobs(1);
+    SeriesJob& s = jobs[0];
+    s.T = ctx->T.p;
+    s.n = n;
+    s.minL = minL;
+    s.maxL = maxL;
+    s.K = topK;
+    s.exclusive = o.exclusive_topk != 0;
+    s.W = std::max(1, o.batch_lengths);
+    s.heat = out_heatmap ? heat.p : nullptr;
+    s.hw = hw;
+    s.count_dev = cnt.p;
+    palmad_status st = run_jobs(ctx, jobs, o);
+    std::vector<int64_t> counts(L);
+    if (st == PALMAD_OK) {
+        cudaError_t e = cudaMemcpyAsync(counts.data(), cnt.p, L * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && out_heatmap)
+            e = cudaMemcpyAsync(out_heatmap, heat.p, size_t(L) * hw * sizeof(float), cudaMemcpyDeviceToHost,
+                                ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = fail(ctx, PALMAD_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
+        tcollect(ctx);
     }
-    std::memcpy(out_idx, lo.idx.data(), lo.idx.size() * sizeof(int64_t));
-    std::memcpy(out_nndist, lo.nn.data(), lo.nn.size() * sizeof(double));
-    if (out_count) std::memcpy(out_count, lo.count.data(), L * sizeof(int64_t));
-    if (out_r) std::memcpy(out_r, lo.r.data(), L * sizeof(double));
-    return PALMAD_OK;
+    if (st == PALMAD_OK) {
+        std::memcpy(out_idx, s.idx.data(), s.idx.size() * sizeof(int64_t));
+        std::memcpy(out_nndist, s.nn.data(), s.nn.size() * sizeof(double));
+        if (out_count) std::memcpy(out_count, counts.data(), L * sizeof(int64_t));
+        if (out_r) std::memcpy(out_r, s.r_final.data(), L * sizeof(double));
+        count_discords(ctx, counts);
+    }
+    release(cnt);
+    release(heat);
+    return st;
 }
 
 palmad_status palmad_find_discords_batch(palmad_ctx* ctx, int32_t count, const float* const* T, const int64_t* n,
@@ -756,38 +1051,61 @@ palmad_status palmad_find_discords_batch(palmad_ctx* ctx, int32_t count, const f
         CKS(check_args(ctx, n[s], minL[s], maxL[s], topK));
         if (!T[s] || !out_idx[s] || !out_nndist[s]) return fail(ctx, PALMAD_ERR_ARG, "null series or output pointer");
     }
-    palmad_stats total{};
-    total.struct_size = sizeof(palmad_stats);
+    palmad_options o;
+    CKS(read_options(ctx, opt, o));
+    CKS(begin_call(ctx, o));
+    if (count == 0) return PALMAD_OK;
+    // all series in one device buffer, each on a 16-byte boundary
+    std::vector<int64_t> off(count);
+    int64_t tot = 0;
     for (int32_t s = 0; s < count; ++s) {
-        const int32_t L = maxL[s] - minL[s] + 1;
-        std::vector<int64_t> idx(size_t(L) * topK), cnt(L);
-        std::vector<double> nn(size_t(L) * topK), rr(L);
-        CKS(palmad_find_discords(ctx, T[s], n[s], minL[s], maxL[s], topK, opt, idx.data(), nn.data(), cnt.data(),
-                                 rr.data(), nullptr));
-        std::memcpy(out_idx[s], idx.data(), idx.size() * sizeof(int64_t));
-        std::memcpy(out_nndist[s], nn.data(), nn.size() * sizeof(double));
-        if (out_count && out_count[s]) std::memcpy(out_count[s], cnt.data(), L * sizeof(int64_t));
-        if (out_r && out_r[s]) std::memcpy(out_r[s], rr.data(), L * sizeof(double));
-        const palmad_stats& st = ctx->stats;
-        total.lengths += st.lengths;
-        total.drag_calls += st.drag_calls;
-        total.device_passes += st.device_passes;
-        total.select_pairs += st.select_pairs;
-        total.refine_pairs += st.refine_pairs;
-        total.fp64_pairs += st.fp64_pairs;
-        total.survivors += st.survivors;
-        total.discords += st.discords;
-        total.max_fp32_rho_err = std::max(total.max_fp32_rho_err, st.max_fp32_rho_err);
-        total.select_flops += st.select_flops;
-        total.refine_flops += st.refine_flops;
-        total.sweep_flops += st.sweep_flops;
-        for (int k = 0; k < PALMAD_K_COUNT; ++k) {
-            total.launches[k] += st.launches[k];
-            total.kernel_ms[k] += st.kernel_ms[k];
-        }
+        off[s] = tot;
+        tot += ((n[s] + 3) / 4) * 4;
     }
-    ctx->stats = total;
-    return PALMAD_OK;
+    int64_t Ltot = 0;
+    for (int32_t s = 0; s < count; ++s) Ltot += maxL[s] - minL[s] + 1;
+    CKS(ensure(ctx, ctx->T, size_t(tot)));
+    for (int32_t s = 0; s < count; ++s)
+        CK(cudaMemcpyAsync(ctx->T.p + off[s], T[s], size_t(n[s]) * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    DBuf<int64_t> cnt;
+    CKS(ensure(ctx, cnt, size_t(Ltot)));
+    std::vector<SeriesJob> jobs(count);
+    int64_t coff = 0;
+    for (int32_t s = 0; s < count; ++s) {
+        SeriesJob& j = jobs[s];
+        j.T = ctx->T.p + off[s];
+        j.n = n[s];
+        j.minL = minL[s];
+        j.maxL = maxL[s];
+        j.K = topK;
+        j.exclusive = o.exclusive_topk != 0;
+        j.W = std::max(1, o.batch_lengths);
+        j.count_dev = cnt.p + coff;
+        coff += maxL[s] - minL[s] + 1;
+    }
+    palmad_status st = run_jobs(ctx, jobs, o);
+    std::vector<int64_t> counts(size_t(Ltot > 0 ? Ltot : 1));
+    if (st == PALMAD_OK) {
+        cudaError_t e = cudaMemcpyAsync(counts.data(), cnt.p, Ltot * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = fail(ctx, PALMAD_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
+        tcollect(ctx);
+    }
+    if (st == PALMAD_OK) {
+        coff = 0;
+        for (int32_t s = 0; s < count; ++s) {
+            const SeriesJob& j = jobs[s];
+            const int32_t L = j.maxL - j.minL + 1;
+            std::memcpy(out_idx[s], j.idx.data(), j.idx.size() * sizeof(int64_t));
+            std::memcpy(out_nndist[s], j.nn.data(), j.nn.size() * sizeof(double));
+            if (out_count && out_count[s]) std::memcpy(out_count[s], counts.data() + coff, L * sizeof(int64_t));
+            if (out_r && out_r[s]) std::memcpy(out_r[s], j.r_final.data(), L * sizeof(double));
+            coff += L;
+        }
+        count_discords(ctx, counts);
+    }
+    release(cnt);
+    return st;
 }
 
 palmad_status palmad_drag(palmad_ctx* ctx, const float* T, int64_t n, int32_t m, double r, const palmad_options* opt,
@@ -795,6 +1113,7 @@ palmad_status palmad_drag(palmad_ctx* ctx, const float* T, int64_t n, int32_t m,
     if (!ctx) return PALMAD_ERR_ARG;
     if (m < 3) return fail(ctx, PALMAD_ERR_ARG, "m must be >= 3");
     if (n < 2 * int64_t(m)) return fail(ctx, PALMAD_ERR_ARG, "n must be >= 2*m");
+    if (n > (int64_t(1) << 30)) return fail(ctx, PALMAD_ERR_UNSUPPORTED, "n above 2^30 is not supported");
     if (!T || !out_count || cap < 0 || (cap > 0 && (!out_idx || !out_nndist)))
         return fail(ctx, PALMAD_ERR_ARG, "bad pointer or cap");
     if (!std::isfinite(r)) return fail(ctx, PALMAD_ERR_ARG, "r must be finite");
@@ -803,30 +1122,49 @@ palmad_status palmad_drag(palmad_ctx* ctx, const float* T, int64_t n, int32_t m,
     CKS(begin_call(ctx, o));
     CKS(ensure(ctx, ctx->T, size_t(n)));
     CK(cudaMemcpyAsync(ctx->T.p, T, size_t(n) * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    Job job{};
-    job.T = ctx->T.p;
-    job.n = n;
-    job.minL = m;
-    job.maxL = m;
-    job.K = 1;
-    job.exclusive = true;
-    job.opt = o;
-    CKS(reserve(ctx, job));
-    CKS(prepare_length(ctx, job, m, true));
-    DragResult res;
-    CKS(drag_call(ctx, job, r, res));
-    ctx->stats.drag_calls += 1;
+    if (ctx->sets.empty()) ctx->sets.resize(1);
+    LaneSet& S = ctx->sets[0];
+    const int64_t N = n - m + 1;
+    CKS(ensure_set(ctx, S, N));
+    CKS(ensure(ctx, ctx->init_flags, 1));
+    CK(cudaMemsetAsync(ctx->init_flags.p, 0, sizeof(int32_t), ctx->stream));
+    LAUNCH(PALMAD_K_STATS, launch_stats_init(ctx->T.p, n, m, S.mu.p, S.var.p, ctx->init_flags.p, ctx->stream));
+    int32_t flag = 0;
+    CK(cudaMemcpyAsync(&flag, ctx->init_flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CKS(sync(ctx));
+    if (flag & 1) return fail(ctx, PALMAD_ERR_NONFINITE, "T holds a NaN or an infinity");
+    std::vector<PassLane> req(1);
+    Lane& L = req[0].lane;
+    L = Lane{};
+    L.T = ctx->T.p;
+    L.n = n;
+    L.m = m;
+    L.N = N;
+    L.mu = S.mu.p; L.var = S.var.p; L.win = S.win.p; L.bits0 = S.bits0.p; L.bits = S.bits.p;
+    L.surv = S.surv.p; L.slot_of = S.slot_of.p; L.scount = S.scount.p; L.didx = S.didx.p; L.dnn = S.dnn.p;
+    L.stats_mode = 2;
+    L.mu_src = S.mu.p;
+    L.var_src = S.var.p;
+    L.r = r;
+    L.prune = r > 0.0 ? 1 : 0;
+    L.rho_thr = float(1.0 - r * r / (2.0 * m));
+    L.band = float(o.band_rel * r * r / m);
+    req[0].state = LaneState{};
+    PassOut out;
+    CKS(run_pass(ctx, req, 1, true, o, out));
+    const int64_t cnt = out.st[0].dcount;
+    ctx->stats.drag_calls = 1;
     ctx->stats.lengths = 1;
-    ctx->stats.discords = res.count;
-    const int64_t k = std::min<int64_t>(cap, res.count);
+    ctx->stats.discords = cnt;
+    const int64_t k = std::min<int64_t>(cap, cnt);
     if (k > 0) {
         std::vector<int32_t> idx(k);
-        CK(cudaMemcpyAsync(idx.data(), ctx->didx.p, k * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaMemcpyAsync(out_nndist, ctx->dnn.p, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(idx.data(), S.didx.p, k * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(out_nndist, S.dnn.p, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         CKS(sync(ctx));
         for (int64_t q = 0; q < k; ++q) out_idx[q] = idx[q];
     }
-    *out_count = res.count;
+    *out_count = cnt;
     return PALMAD_OK;
 }
 

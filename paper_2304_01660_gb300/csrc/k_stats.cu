@@ -1,6 +1,6 @@
 // Window statistics: mean and deviation of every length-m window (Eq. 4),
 // carried from m to m+1 by the recurrences of Eq. 7-8 (Sec. 3.1.1), plus the
-// per-window FP32 records the pair kernels read and the candidate bitmap.
+// per-window FP32 records the pair kernels read and the candidate bitmaps.
 #include "palmad_dev.cuh"
 
 namespace palmad {
@@ -69,56 +69,72 @@ __device__ __forceinline__ void advance_one(double mu_o, double var_o, float t_n
     var_n = mm1 * inv_m * (var_o + d * d * inv_m);
 }
 
-__global__ void k_stats_step(const StatsArgs a) {
-    const int64_t N = a.n - a.m + 1;
-    const int64_t P = (N + 31) / 32;
+// Statistics of every lane of a pass.  blockIdx.y selects a chain of lanes
+// (consecutive lengths of one series); a thread owns a fixed set of window
+// indices i and walks the chain, so lane l+1 advances (Eq. 7-8) from the
+// values lane l just wrote at the same i.  Per lane it writes the FP64
+// mean / variance, the FP32 window records, the candidate bitmaps and the
+// maxima behind the FP32 error bound.
+__global__ void k_stats(const Pass p, const int32_t* __restrict__ chain_first) {
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    const int32_t m = a.m;
-    bool any_flat = false;
-    float amax = 0.f, bmax = 0.f;
-    for (int64_t i = tid; i < N; i += stride) {
-        double mu_i, var_i;
-        const float t_add = a.T[i + m - 1];
-        if (a.advance) advance_one(a.mu_old[i], a.var_old[i], t_add, m, mu_i, var_i);
-        else { mu_i = a.mu_old[i]; var_i = a.var_old[i]; }
-        a.mu[i] = mu_i;
-        a.var[i] = var_i;
-        const double sd = sqrt(var_i);
-        const bool flat = sd <= kFlatRel * fabs(mu_i);
-        any_flat |= flat;
-        float df = 0.f, dg = 0.f;
-        if (i >= 1) {
-            // mu_{i-1} = mu_i - (t[i+m-1] - t[i-1]) / m for windows of one length
-            const double diff = double(t_add) - double(a.T[i - 1]);
-            const double mu_p = mu_i - diff / double(m);
-            df = float(0.5 * diff);
-            dg = float((double(t_add) - mu_i) + (double(a.T[i - 1]) - mu_p));
-        }
-        const float inv = flat ? 0.f : rsqrtf(float(double(m) * var_i));
-        a.win[i] = make_float4(df, dg, inv, float(mu_i));
-        amax = fmaxf(amax, fabsf(df) * inv);
-        bmax = fmaxf(bmax, fabsf(dg) * inv);
-    }
+    for (int l = chain_first[blockIdx.y];; ++l) {
+        const Lane& L = p.lanes[l];
+        LaneState& S = p.st[l];
+        const int64_t N = L.N;
+        const int32_t m = L.m;
+        const int64_t P = (N + 31) / 32;
+        const float* T = L.T;
+        if (L.stats_mode != 0) {
+            bool any_flat = false;
+            float amax = 0.f, bmax = 0.f;
+            for (int64_t i = tid; i < N; i += stride) {
+                double mu_i, var_i;
+                const float t_add = T[i + m - 1];
+                if (L.stats_mode == 1) advance_one(L.mu_src[i], L.var_src[i], t_add, m, mu_i, var_i);
+                else { mu_i = L.mu_src[i]; var_i = L.var_src[i]; }
+                L.mu[i] = mu_i;
+                L.var[i] = var_i;
+                const bool flat = sqrt(var_i) <= kFlatRel * fabs(mu_i);
+                any_flat |= flat;
+                float df = 0.f, dg = 0.f;
+                if (i >= 1) {
+                    // mu_{i-1} = mu_i - (t[i+m-1] - t[i-1]) / m for windows of one length
+                    const double diff = double(t_add) - double(T[i - 1]);
+                    const double mu_p = mu_i - diff / double(m);
+                    df = float(0.5 * diff);
+                    dg = float((double(t_add) - mu_i) + (double(T[i - 1]) - mu_p));
+                }
+                const float inv = flat ? 0.f : rsqrtf(float(double(m) * var_i));
+                L.win[i] = make_float4(df, dg, inv, float(mu_i));
+                amax = fmaxf(amax, fabsf(df) * inv);
+                bmax = fmaxf(bmax, fabsf(dg) * inv);
+            }
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-        bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(&a.ab[0], __float_as_uint(amax));
-        atomicMax(&a.ab[1], __float_as_uint(bmax));
-    }
-    // Candidate bitmap: a window starts alive iff it has a non-self match.
-    for (int64_t w = tid; w < P; w += stride) {
-        uint32_t word = 0;
-        for (int b = 0; b < 32; ++b) {
-            const int64_t i = w * 32 + b;
-            if (i < N && (i + m <= N - 1 || i - m >= 0)) word |= 1u << b;
+            for (int o = 16; o >= 1; o >>= 1) {
+                amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+                bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+            }
+            if ((threadIdx.x & 31) == 0) {
+                atomicMax(&S.ab[0], __float_as_uint(amax));
+                atomicMax(&S.ab[1], __float_as_uint(bmax));
+            }
+            if (any_flat) atomicOr(&S.flags, 2);
+            // Candidate bitmap: a window starts alive iff it has a non-self match.
+            for (int64_t w = tid; w < P; w += stride) {
+                uint32_t word = 0;
+                for (int b = 0; b < 32; ++b) {
+                    const int64_t i = w * 32 + b;
+                    if (i < N && (i + m <= N - 1 || i - m >= 0)) word |= 1u << b;
+                }
+                L.bits0[w] = word;
+                L.bits[w] = word;
+            }
+        } else {
+            for (int64_t w = tid; w < P; w += stride) L.bits[w] = L.bits0[w];
         }
-        a.bits[w] = word;
+        if (!L.chain_next) break;
     }
-    if (any_flat) atomicOr(a.flags, 2);
 }
 
 }  // namespace
@@ -133,13 +149,19 @@ cudaError_t launch_stats_init(const float* T, int64_t n, int32_t m, double* mu, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_stats_step(const StatsArgs& a, cudaStream_t s) {
-    const int64_t N = a.n - a.m + 1;
+cudaError_t launch_stats(const Pass& p, const int32_t* chain_first, int32_t nchains, int64_t nmax, cudaStream_t s) {
+    if (nchains <= 0) return cudaSuccess;
     const int block = 256;
-    int64_t grid = (N + block - 1) / block;
-    if (grid > 152 * 16) grid = 152 * 16;
-    k_stats_step<<<int(grid), block, 0, s>>>(a);
+    int64_t gx = (nmax + block - 1) / block;
+    if (gx > 152 * 8) gx = 152 * 8;
+    k_stats<<<dim3(unsigned(gx), unsigned(nchains)), block, 0, s>>>(p, chain_first);
     return cudaGetLastError();
+}
+
+int sm_count(int device) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return sms;
 }
 
 }  // namespace palmad

@@ -50,12 +50,20 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Fields of the lane a work item belongs to.
+struct LaneView {
+    const float* T;
+    int64_t n, N;
+    int32_t m;
+    const WinRec* win;
+};
+
 // Start the asynchronous copy of chunk c0's series slice and column records
 // into buffer b (zero fill past the ends of T and of the windows).  T and
 // win are 16-byte aligned and c0 is a multiple of 32.
-__device__ __forceinline__ void issue_chunk(const SweepArgs& a, const WarpSmem& sm, int b, int64_t c0, int kp,
-                                            int lane) {
-    float* tw = sm.tw + b * (kp + 32);
+__device__ __forceinline__ void issue_chunk(const LaneView& a, const WarpSmem& sm, int kps, int b, int64_t c0,
+                                            int kp, int lane) {
+    float* tw = sm.tw + b * (kps + 32);
     for (int x = lane * 4; x < kp + 32; x += 128) {
         const int64_t t = c0 + x;
         const int64_t rem = a.n - t;
@@ -91,10 +99,10 @@ __device__ __forceinline__ float reduce_scatter32(float (&acc)[32], int lane) {
 
 // Top-row dot products cov(top, c0 + lane) of one chunk from the staged
 // buffer b (series slice minus the offset b0 = mu of column c0).
-__device__ __forceinline__ void chunk_seeds(const SweepArgs& a, const WarpSmem& sm, int b, int64_t c0, float suma,
-                                            int kp, int lane) {
+__device__ __forceinline__ void chunk_seeds(const LaneView& a, const WarpSmem& sm, int kps, int b, int64_t c0,
+                                            float suma, int kp, int lane) {
     const int s4 = kp / 32;
-    float* tw = sm.tw + b * (kp + 32);
+    float* tw = sm.tw + b * (kps + 32);
     const float4* cr = sm.colrec + b * 32;
     const float b0 = cr[0].w;
     for (int x = lane; x < kp + 32; x += 32) tw[x] -= b0;
@@ -128,7 +136,7 @@ __device__ __forceinline__ void chunk_seeds(const SweepArgs& a, const WarpSmem& 
 // cov(r0 + d, ja) for d < D: direct dot products of this lane's rows with
 // column ja (centred column window x, rows offset by b0 = mu of row r0).
 template <int D>
-__device__ __forceinline__ void first_col_seeds(const SweepArgs& a, int64_t r0, int64_t ja, float (&cov)[D]) {
+__device__ __forceinline__ void first_col_seeds(const LaneView& a, int64_t r0, int64_t ja, float (&cov)[D]) {
     const int32_t m = a.m;
     const float mux = a.win[ja].w;
     const float b0 = (r0 < a.N) ? a.win[r0].w : 0.f;
@@ -163,39 +171,56 @@ __device__ __forceinline__ void first_col_seeds(const SweepArgs& a, int64_t r0, 
 }
 
 template <int D, bool REFINE>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const SweepArgs a) {
+__global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const Pass p) {
     constexpr int H = 32 * D;
     extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int32_t m = a.m;
-    const int kp = ((m + 127) / 128) * 128;
-    float* base = smem + warp_smem_floats(kp) * wid;
-    const WarpSmem sm{base, base + kp, reinterpret_cast<float4*>(base + kp + 2 * (kp + 32)),
-                      base + kp + 2 * (kp + 32) + 256};
-
-    const int64_t N = a.N;
-    const float rho_prune = rho_prune_of(a.th);
-    const int64_t nstrips = (N + H - 1) / H;
-    const int64_t nseg = REFINE ? (N + a.seg - 1) / a.seg : 1;
-    const int64_t nitems = REFINE ? int64_t(*a.nref) * nseg : nstrips;
+    const int kps = ((p.kpad_max + 127) / 128) * 128;  // smem stride (largest lane)
+    float* base = smem + warp_smem_floats(kps) * wid;
+    const WarpSmem sm{base, base + kps, reinterpret_cast<float4*>(base + kps + 2 * (kps + 32)),
+                      base + kps + 2 * (kps + 32) + 256};
+    int64_t* strip_base = reinterpret_cast<int64_t*>(smem + warp_smem_floats(kps) * kWarpsPerCta);
+    if (!REFINE) {
+        for (int l = threadIdx.x; l < p.nl; l += blockDim.x) strip_base[l] = p.lanes[l].strip_base;
+        __syncthreads();
+    }
+    const int64_t nseg = REFINE ? (p.nmax + p.seg - 1) / p.seg : 1;
+    const int64_t nitems = REFINE ? int64_t(*p.nref) * nseg : p.sel_items;
     unsigned long long pairs = 0, seeds = 0;
 
     for (;;) {
         int64_t item = 0;
-        if (lane == 0) item = atomicAdd(a.work, 1);
+        if (lane == 0) item = atomicAdd(p.work + (REFINE ? 2 : 0), 1);
         item = __shfl_sync(kFull, item, 0);
         if (item >= nitems) break;
-        int64_t s, ja, jb;
+        int l;
+        int64_t s;
         if (REFINE) {
-            s = a.strips[item / nseg];
-            ja = (item % nseg) * a.seg;
-            jb = min64(N, ja + a.seg);
+            const int2 e = p.strips[item / nseg];
+            l = e.x;
+            s = e.y;
         } else {
-            s = item;
+            l = lane_of(strip_base, p.nl, item);
+            s = item - strip_base[l];
+        }
+        const Lane& Lg = p.lanes[l];
+        const LaneView a{Lg.T, Lg.n, Lg.N, Lg.m, Lg.win};
+        const int32_t m = a.m;
+        const int64_t N = a.N;
+        const int kp = ((m + 127) / 128) * 128;
+        const float rho_prune = rho_prune_of(Lg, p.st[l]);
+        int64_t ja, jb;
+        if (REFINE) {
+            ja = (item % nseg) * p.seg;
+            if (ja >= N) continue;
+            jb = min64(N, ja + p.seg);
+        } else {
             ja = s * H + m;
             if (ja >= N) continue;  // no window to the right: column marks / refine decide these rows
-            jb = min64(N, s * H + H - 1 + m + a.cap);
+            jb = min64(N, s * H + H - 1 + m + p.cap);
         }
+        uint32_t* bits = Lg.bits;
+        const int32_t* slot_of = Lg.slot_of;
         const int64_t i0 = s * H;
         const int64_t r0 = i0 + int64_t(lane) * D;
 
@@ -216,18 +241,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const SweepArgs a) 
             rmax[d] = -kInf;
             slot[d] = -1;
             if (REFINE && i < N) {
-                slot[d] = a.slot_of[i];
-                if (slot[d] >= 0 && !__ldcg(&a.dead[slot[d]])) alive |= 1u << d;
+                slot[d] = slot_of[i];
+                if (slot[d] >= 0 && !__ldcg(&p.dead[slot[d]])) alive |= 1u << d;
             }
         }
         const int64_t wrd = r0 >> 5;
         const int sh = int(r0 & 31);
         const uint32_t dmask = (D == 32) ? kFull : ((1u << D) - 1u);
-        if (!REFINE) alive = (r0 < N) ? ((__ldcg(&a.bits[wrd]) >> sh) & dmask) : 0u;
+        if (!REFINE) alive = (r0 < N) ? ((__ldcg(&bits[wrd]) >> sh) & dmask) : 0u;
         if (!__any_sync(kFull, alive)) continue;
 
         const int64_t cfirst = ja & ~int64_t(31);
-        issue_chunk(a, sm, 0, cfirst, kp, lane);
+        issue_chunk(a, sm, kps, 0, cfirst, kp, lane);
 
         // Centred top-row window and its sum (FP32; the sum absorbs the
         // rounding of mu so the seed correction is exact to rounding).
@@ -254,16 +279,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const SweepArgs a) 
         for (int64_t c0 = cfirst; c0 < jb; c0 += 32, buf ^= 1) {
             cp_async_wait_all();
             __syncwarp();
-            if (c0 + 32 < jb) issue_chunk(a, sm, buf ^ 1, c0 + 32, kp, lane);
+            if (c0 + 32 < jb) issue_chunk(a, sm, kps, buf ^ 1, c0 + 32, kp, lane);
             // state other warps may have changed, read early and used at the chunk end
             uint32_t gbits = 0, gdead = 0;
-            if (!REFINE && r0 < N) gbits = __ldcg(&a.bits[wrd]);
+            if (!REFINE && r0 < N) gbits = __ldcg(&bits[wrd]);
             if (REFINE) {
 #pragma unroll
                 for (int d = 0; d < D; ++d)
-                    if (((alive >> d) & 1u) && __ldcg(&a.dead[slot[d]])) gdead |= 1u << d;
+                    if (((alive >> d) & 1u) && __ldcg(&p.dead[slot[d]])) gdead |= 1u << d;
             }
-            chunk_seeds(a, sm, buf, c0, suma, kp, lane);
+            chunk_seeds(a, sm, kps, buf, c0, suma, kp, lane);
             const float4* crb = sm.colrec + buf * 32;
             const int steps = int(min64(32, jb - c0));
             const int st0 = int(max64(0, ja - c0));
@@ -315,14 +340,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const SweepArgs a) 
             if (!REFINE) {
                 // Neighbour (column) marks, row deaths, rows killed elsewhere.
                 const uint32_t cw = __reduce_or_sync(kFull, colmask);
-                if (lane == 0 && cw) atomicAnd(&a.bits[c0 >> 5], ~cw);
+                if (lane == 0 && cw) atomicAnd(&bits[c0 >> 5], ~cw);
                 uint32_t newdead = 0;
 #pragma unroll
                 for (int d = 0; d < D; ++d)
                     if (((alive >> d) & 1u) && rmax[d] > thr_r[d]) newdead |= 1u << d;
                 if (newdead) {
                     alive &= ~newdead;
-                    atomicAnd(&a.bits[wrd], ~(newdead << sh));
+                    atomicAnd(&bits[wrd], ~(newdead << sh));
                 }
                 if (r0 < N) alive &= (gbits >> sh) & dmask;
                 if (!__any_sync(kFull, alive)) break;
@@ -333,10 +358,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const SweepArgs a) 
                 for (int d = 0; d < D; ++d) {
                     if (slot[d] >= 0) {
                         const float rho = rmax[d] > -kInf ? rmax[d] * inv_r[d] : -kInf;
-                        a.cmax[int64_t(slot[d]) * a.nchunks + t] = rho;
+                        p.cmax[int64_t(slot[d]) * p.nchunks_max + t] = rho;
                         tmax[d] = fmaxf(tmax[d], rho);
                         if (rmax[d] > thr_r[d]) {
-                            a.dead[slot[d]] = 1;
+                            p.dead[slot[d]] = 1;
                             alive &= ~(1u << d);
                         }
                     }
@@ -352,42 +377,37 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const SweepArgs a) 
         if (REFINE) {
 #pragma unroll
             for (int d = 0; d < D; ++d)
-                if (slot[d] >= 0 && tmax[d] > -kInf) atomicMax(&a.gmax[slot[d]], enc_f32(tmax[d]));
+                if (slot[d] >= 0 && tmax[d] > -kInf) atomicMax(&p.gmax[slot[d]], enc_f32(tmax[d]));
         }
     }
-    if (lane == 0 && pairs) atomicAdd(a.pairs, pairs);
-    if (lane == 0 && seeds) atomicAdd(a.seeds, seeds);
+    if (lane == 0 && pairs) atomicAdd(p.pairs + (REFINE ? 4 : 0), pairs);
+    if (lane == 0 && seeds) atomicAdd(p.pairs + (REFINE ? 5 : 3), seeds);
 }
 
-size_t sweep_smem(int32_t m) {
-    const size_t kp = ((m + 127) / 128) * 128;
-    return sizeof(float) * (kp + 2 * (kp + 32) + 2 * 128 + 32) * kWarpsPerCta;
+size_t sweep_smem(const Pass& p) {
+    const size_t kp = ((p.kpad_max + 127) / 128) * 128;
+    return sizeof(float) * (kp + 2 * (kp + 32) + 2 * 128 + 32) * kWarpsPerCta + sizeof(int64_t) * size_t(p.nl);
 }
 
 template <bool REFINE>
-cudaError_t launch_sweep_impl(const SweepArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_sweep_impl(const Pass& p, int grid, cudaStream_t s) {
     constexpr int D = 8;
-    const size_t sm = sweep_smem(a.m);
+    static_assert(32 * D == kStripH, "strip height");
+    const size_t sm = sweep_smem(p);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_sweep<D, REFINE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         if (e != cudaSuccess) return e;
     }
-    k_sweep<D, REFINE><<<grid, kWarpsPerCta * 32, sm, s>>>(a);
+    k_sweep<D, REFINE><<<grid, kWarpsPerCta * 32, sm, s>>>(p);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int sweep_grid(int device) {
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    return sms * 4;
-}
+cudaError_t launch_select(const Pass& p, int grid, cudaStream_t s) { return launch_sweep_impl<false>(p, grid, s); }
 
-cudaError_t launch_select(const SweepArgs& a, int grid, cudaStream_t s) { return launch_sweep_impl<false>(a, grid, s); }
-
-cudaError_t launch_refine_sweep(const SweepArgs& a, int grid, cudaStream_t s) {
-    return launch_sweep_impl<true>(a, grid, s);
+cudaError_t launch_refine_sweep(const Pass& p, int grid, cudaStream_t s) {
+    return launch_sweep_impl<true>(p, grid, s);
 }
 
 }  // namespace palmad

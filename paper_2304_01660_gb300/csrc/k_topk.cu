@@ -1,11 +1,14 @@
-// Per-length results (Sec. 2.2 and Sec. 5):
-//  k_gather  range discords of this DRAG call: live survivors whose FP64
-//            nearest-neighbour distance is >= r (Sec. 2.1), appended in
-//            ascending index order to the discord list.
-//  k_topk    greedy top-K over the list: largest distance first (ties to
-//            the lower index), optionally keeping picks >= m apart; one CTA,
-//            warp-shuffle argmax per round.
-//  k_heat    heatmap row of Eq. 10: nnDist^2 / (2m) at every discord.
+// Per-lane results (Sec. 2.2 and Sec. 5):
+//  k_round_reset  clears the window -> slot map and the per-strip survivor
+//                 counts of every lane before a refine round.
+//  k_gather       range discords of the lane: live survivors whose FP64
+//                 nearest-neighbour distance is >= r (Sec. 2.1), appended in
+//                 ascending index order to the lane's discord list.
+//  k_topk         greedy top-K over the lane's list: largest distance first
+//                 (ties to the lower index), optionally keeping picks >= m
+//                 apart; one CTA per lane, warp-shuffle argmax per round.
+//  k_finalize     at the final r of each lane: the number of range
+//                 discords and the heatmap row of Eq. 10 (nnDist^2 / (2m)).
 #include "palmad_dev.cuh"
 
 namespace palmad {
@@ -15,18 +18,32 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 
-__global__ void __launch_bounds__(1024) k_gather(const GatherArgs a) {
+__global__ void k_round_reset(const Pass p) {
+    const Lane& L = p.lanes[blockIdx.y];
+    const int64_t ns = (L.N + kStripH - 1) / kStripH;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < L.N; i += int64_t(gridDim.x) * blockDim.x) {
+        L.slot_of[i] = -1;
+        if (i < ns) L.scount[i] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_gather(const Pass p) {
     __shared__ int32_t warp_tot[32];
     __shared__ int32_t base_s;
+    const int l = blockIdx.x;
+    const Lane& L = p.lanes[l];
+    LaneState& S = p.st[l];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) base_s = *a.count;
-    const int64_t per = (int64_t(a.ns) + blockDim.x - 1) / blockDim.x;
-    const int64_t s0 = tid * per, s1 = min64(a.ns, s0 + per);
+    const int32_t ns = L.k_hi - L.k_lo;
+    if (tid == 0) base_s = S.dcount;
+    const int64_t per = (int64_t(ns) + blockDim.x - 1) / blockDim.x;
+    const int64_t s0 = tid * per, s1 = min64(ns, s0 + per);
     auto is_discord = [&](int64_t s) -> bool {
-        if (a.dead[s]) return false;
-        const unsigned long long b = a.nn2[s];
+        const int64_t g = L.slot_base + s;
+        if (p.dead[g]) return false;
+        const unsigned long long b = p.nn2[g];
         if (b >= kInfBits) return false;
-        return a.r <= 0.0 || sqrt(__longlong_as_double(static_cast<long long>(b))) >= a.r;
+        return L.r <= 0.0 || sqrt(__longlong_as_double(static_cast<long long>(b))) >= L.r;
     };
     int32_t cnt = 0;
     for (int64_t s = s0; s < s1; ++s) cnt += is_discord(s);
@@ -47,14 +64,15 @@ __global__ void __launch_bounds__(1024) k_gather(const GatherArgs a) {
             if (lane >= o) s += u;
         }
         warp_tot[lane] = s - v;
-        if (lane == 31) *a.count = base_s + s;
+        if (lane == 31) S.dcount = base_s + s;
     }
     __syncthreads();
     int32_t off = base_s + warp_tot[wid] + incl - cnt;
     for (int64_t s = s0; s < s1; ++s) {
         if (!is_discord(s)) continue;
-        a.out_idx[off] = a.surv[s];
-        a.out_nn[off] = sqrt(__longlong_as_double(static_cast<long long>(a.nn2[s])));
+        const int64_t g = L.slot_base + s;
+        L.didx[off] = p.slot_win[g];
+        L.dnn[off] = sqrt(__longlong_as_double(static_cast<long long>(p.nn2[g])));
         ++off;
     }
 }
@@ -64,28 +82,34 @@ __device__ __forceinline__ bool better(double nn, int32_t idx, double bnn, int32
     return nn > bnn || (nn == bnn && idx < bidx);
 }
 
-__global__ void __launch_bounds__(1024) k_topk(const TopkArgs a) {
-    __shared__ int32_t picks[1024];
+__global__ void __launch_bounds__(1024) k_topk(const Pass p) {
+    __shared__ int32_t picks[kMaxK];
     __shared__ double wbest_nn[32];
     __shared__ int32_t wbest_idx[32];
     __shared__ int32_t wbest_pos[32];
     __shared__ int done_s;
+    const int l = blockIdx.x;
+    const Lane& L = p.lanes[l];
+    LaneState& S = p.st[l];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int32_t count = *a.count;
+    const int32_t count = S.dcount;
+    const int32_t m = L.m;
+    int64_t* pidx = p.pick_idx + int64_t(l) * p.K;
+    double* pnn = p.pick_nn + int64_t(l) * p.K;
     int got = 0;
-    for (int round = 0; round < a.K; ++round) {
+    for (int round = 0; round < p.K; ++round) {
         double bnn = -1.0;
         int32_t bidx = 0x7fffffff, bpos = -1;
-        for (int32_t p = tid; p < count; p += blockDim.x) {
-            const int32_t idx = a.idx[p];
-            const double nn = a.nn[p];
+        for (int32_t q = tid; q < count; q += blockDim.x) {
+            const int32_t idx = L.didx[q];
+            const double nn = L.dnn[q];
             if (!better(nn, idx, bnn, bidx)) continue;
             bool ok = true;
-            for (int q = 0; q < got && ok; ++q) {
-                const int32_t d = idx - picks[q];
-                ok = a.exclusive ? (d >= a.m || d <= -a.m) : (d != 0);
+            for (int r = 0; r < got && ok; ++r) {
+                const int32_t d = idx - picks[r];
+                ok = p.exclusive ? (d >= m || d <= -m) : (d != 0);
             }
-            if (ok) { bnn = nn; bidx = idx; bpos = p; }
+            if (ok) { bnn = nn; bidx = idx; bpos = q; }
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
@@ -106,44 +130,63 @@ __global__ void __launch_bounds__(1024) k_topk(const TopkArgs a) {
             done_s = pos < 0;
             if (pos >= 0) {
                 picks[got] = idx;
-                a.pick_idx[got] = idx;
-                a.pick_nn[got] = nn;
+                pidx[got] = idx;
+                pnn[got] = nn;
             }
         }
         __syncthreads();
         if (done_s) break;
         ++got;
     }
-    for (int q = got + tid; q < a.K; q += blockDim.x) {
-        a.pick_idx[q] = -1;
-        a.pick_nn[q] = 0.0;
+    for (int q = got + tid; q < p.K; q += blockDim.x) {
+        pidx[q] = -1;
+        pnn[q] = 0.0;
     }
+    if (tid == 0) S.got = got;
 }
 
-__global__ void k_heat(const HeatArgs a) {
-    const int32_t count = *a.count;
-    const double inv2m = 1.0 / (2.0 * a.m);
-    for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < count; p += gridDim.x * blockDim.x) {
-        const double nn = a.nn[p];
-        a.row[a.idx[p]] = float(nn * nn * inv2m);
+__global__ void k_finalize(const Pass p) {
+    const int l = blockIdx.y;
+    const Lane& L = p.lanes[l];
+    LaneState& S = p.st[l];
+    const int32_t count = S.dcount;
+    const double inv2m = 1.0 / (2.0 * L.m);
+    int32_t c = 0;
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+        const double nn = L.dnn[q];
+        if (L.r > 0.0 && nn < L.r) continue;
+        ++c;
+        if (L.heat) L.heat[L.didx[q]] = float(nn * nn * inv2m);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0 && c) {
+        atomicAdd(&S.count_final, c);
+        if (L.count_out) atomicAdd(reinterpret_cast<unsigned long long*>(L.count_out), (unsigned long long)c);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s) {
-    if (a.ns <= 0) return cudaSuccess;
-    k_gather<<<1, 1024, 0, s>>>(a);
+cudaError_t launch_round_reset(const Pass& p, cudaStream_t s) {
+    int64_t gx = (p.nmax + 255) / 256;
+    if (gx > 64) gx = 64;
+    k_round_reset<<<dim3(unsigned(gx), unsigned(p.nl)), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s) {
-    k_topk<<<1, 1024, 0, s>>>(a);
+cudaError_t launch_gather(const Pass& p, cudaStream_t s) {
+    k_gather<<<p.nl, 1024, 0, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_heat(const HeatArgs& a, cudaStream_t s) {
-    k_heat<<<152, 256, 0, s>>>(a);
+cudaError_t launch_topk(const Pass& p, cudaStream_t s) {
+    k_topk<<<p.nl, 1024, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Pass& p, cudaStream_t s) {
+    k_finalize<<<dim3(8, unsigned(p.nl)), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

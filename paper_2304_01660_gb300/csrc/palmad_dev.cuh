@@ -6,6 +6,11 @@
 // form: with cov(i, j) = sum_k (t[i+k] - mu_i)(t[j+k] - mu_j),
 //     rho = cov / (m sigma_i sigma_j),   ED^2_norm = 2m (1 - rho).
 // Every kernel works on rho; d < r  <=>  rho > 1 - r^2 / (2m).
+//
+// Work is organised in passes.  A pass holds one or more lanes; a lane is one
+// DRAG evaluation (Algorithm 2): one series, one length m, one threshold r.
+// Every kernel of a pass processes all its lanes, so many lengths (and many
+// series) share each launch.
 #pragma once
 
 #include <cstdint>
@@ -15,6 +20,8 @@ namespace palmad {
 
 constexpr int kWarp = 32;
 constexpr float kInf = __builtin_huge_valf();
+constexpr int kStripH = 256;   // rows per strip of the sweeps (32 lanes x 8)
+constexpr int kMaxK = 1024;    // largest top-K
 
 // Per-window data the FP32 kernels read, one 16-byte record per window:
 //   x = df_i = (t[i+m-1] - t[i-1]) / 2          (Eq. 9 diagonal update)
@@ -37,176 +44,134 @@ __device__ __forceinline__ float dec_f32(uint32_t e) {
     return __uint_as_float(b);
 }
 
-// FP32 error bound on rho and the pruning threshold, evaluated on the device
-// from per-length window maxima the statistics kernel records:
-//   a = |df_i| inv_i,  b = |dg_i| inv_i   (ab[0], ab[1]: float bits, >= 0).
+// One DRAG evaluation.  Written by the host before the pass.
+struct Lane {
+    const float* T;        // series, 16-byte aligned
+    int64_t n;
+    int64_t N;             // windows at this length
+    int32_t m;
+    int32_t kpad;          // m rounded up to 32
+    // statistics (Eq. 4, Eq. 7-8): 0 keep, 1 advance from src (m-1), 2 copy src
+    int32_t stats_mode;
+    int32_t chain_next;    // 1 when the next lane advances from this one
+    const double* mu_src;
+    const double* var_src;
+    double* mu;
+    double* var;
+    WinRec* win;
+    uint32_t* bits0;       // initial candidate bitmap (windows with a non-self match)
+    uint32_t* bits;        // working candidate bitmap
+    int32_t* surv;         // survivors of select, ascending
+    int32_t* slot_of;      // window -> pool slot of this round, -1 otherwise
+    int32_t* scount;       // per strip: survivors this round (+ flat flag in bit 30)
+    int32_t* didx;         // range discords found (ascending), with
+    double* dnn;           //   their FP64 nearest-neighbour distances
+    float* heat;           // heatmap row or nullptr
+    int64_t* count_out;    // where finalize adds the range-discord count, or nullptr
+    // threshold
+    double r;
+    float rho_thr;         // 1 - r^2 / (2m)
+    float band;            // band_rel * r^2 / m
+    int32_t prune;         // 0 when r <= 0
+    int32_t nstrips;       // select strips
+    int64_t strip_base;    // prefix of nstrips over the lanes
+    // refine round: survivors [k_lo, k_hi) occupy pool slots from slot_base
+    int32_t k_lo, k_hi;
+    int32_t slot_base;
+    int32_t pad;
+};
+
+// Per-lane device-written state.
+struct LaneState {
+    int32_t flags;         // |1 non-finite, |2 flat window present
+    uint32_t ab[2];        // max |df| inv, max |dg| inv (float bits), see eps_bound
+    int32_t nsurv;         // survivors of select
+    int32_t dcount;        // range discords gathered
+    int32_t got;           // top-K picks
+    int32_t count_final;   // range discords at the final r (finalize)
+    uint32_t maxerr;       // enc_f32 of the largest |rho_fp32 - rho_fp64| seen
+};
+
+// Everything a pass kernel needs, passed by value.
+struct Pass {
+    const Lane* lanes;
+    LaneState* st;
+    int32_t nl;
+    int32_t K;
+    int32_t exclusive;
+    int32_t seg;           // refine sweep columns per work item (multiple of 256)
+    int64_t cap;           // select columns per strip past its triangle
+    int64_t sel_items;     // total select strips
+    int64_t nmax;          // largest N over the lanes
+    // refine pool (this round)
+    int32_t nslots;        // slots in use this round (64-aligned per lane)
+    int32_t kpad_max;
+    int32_t nchunks_max;   // 32-column chunks of the largest lane
+    int32_t pad;
+    int32_t* slot_lane;    // [slots] lane of each slot
+    int32_t* slot_win;     // [slots] window of each slot, -1 for padding
+    int32_t* route;        // [slots] 0 sweep, 1 direct, -1 none
+    float* acen;           // [slots][kpad_max] centred survivor windows
+    float* asum;           // [slots]
+    uint32_t* gmax;        // [slots] enc_f32 of the maximum rho
+    int32_t* dead;         // [slots]
+    unsigned long long* nn2;  // [slots] FP64 bits of the smallest d^2
+    float* cmax;           // [slots][nchunks_max] maximum rho per 32-column chunk
+    int2* strips;          // (lane, strip) swept by refine
+    int32_t* nref;
+    int32_t* work;         // [8] work counters, zeroed per launch group
+    unsigned long long* pairs;  // [8] 0 select, 1 direct refine, 2 fp64, 3 select seeds,
+                                //     4 sweep refine, 5 sweep seeds
+    int64_t* pick_idx;     // [nl][K]
+    double* pick_nn;       // [nl][K]
+};
+
+// FP32 error bound on rho and the pruning threshold of a lane, from the
+// per-length window maxima the statistics kernel records:
+//   a = |df_i| inv_i,  b = |dg_i| inv_i.
 // A row of a strip sweep is at most H-1 recurrence steps away from a
 // directly computed dot product; each step adds at most
 // 2u + 3u (a_i b_j + a_j b_i) to rho, and a direct dot product of m terms at
 // most ~2mu (1 + 14 a) (centring offsets within 8 columns), u = 2^-24.  The
-// bound below doubles that sum.
-struct Thresh {
-    float rho_thr;   // 1 - r^2 / (2m): d < r  <=>  rho > rho_thr
-    float band;      // band_rel * r^2 / m: the |d - r| < band_rel r floor in rho units
-    int32_t prune;   // 0 when r <= 0 (nothing is ever pruned)
-    int32_t m;
-    int32_t H;       // strip height of the sweeps
-    const uint32_t* ab;
-};
-
-__device__ __forceinline__ float eps_bound(const Thresh& t) {
+// bound doubles that sum.
+__device__ __forceinline__ float eps_bound(int32_t m, const LaneState& s) {
     const float u = 5.9604644775390625e-08f;
-    const float amax = __uint_as_float(__ldcg(&t.ab[0]));
-    const float bmax = __uint_as_float(__ldcg(&t.ab[1]));
-    const float rec = float(t.H - 1) * (2.f + 6.f * amax * bmax);
-    const float dir = 2.f * float(t.m + 4) * (1.f + 14.f * amax);
+    const float amax = __uint_as_float(__ldcg(&s.ab[0]));
+    const float bmax = __uint_as_float(__ldcg(&s.ab[1]));
+    const float rec = float(kStripH - 1) * (2.f + 6.f * amax * bmax);
+    const float dir = 2.f * float(m + 4) * (1.f + 14.f * amax);
     return 2.f * u * (rec + dir + 32.f);
 }
-__device__ __forceinline__ float rho_prune_of(const Thresh& t) {
-    return t.prune ? t.rho_thr + fmaxf(eps_bound(t), t.band) : kInf;
+__device__ __forceinline__ float rho_prune_of(const Lane& L, const LaneState& s) {
+    return L.prune ? L.rho_thr + fmaxf(eps_bound(L.m, s), L.band) : kInf;
 }
 
-struct StatsArgs {
-    const float* T;
-    int64_t n;
-    int32_t m;           // length being prepared
-    int32_t advance;     // 1: Eq. 7-8 from (mu_old, var_old) at m-1; 0: copy
-    const double* mu_old;
-    const double* var_old;
-    double* mu;          // [N] FP64 mean at m
-    double* var;         // [N] FP64 variance at m
-    WinRec* win;         // [N]
-    uint32_t* bits;      // [ceil(N/32)] candidate bitmap, initialised here
-    int32_t* flags;      // [0] |= 1 non-finite, |= 2 flat window present
-    uint32_t* ab;        // [2] max a, max b (float bits) -- see Thresh
-};
-
-// Strip sweeps (select and the recurrence form of refine).
-struct SweepArgs {
-    const float* T;
-    int64_t n;
-    int64_t N;
-    int32_t m;
-    const WinRec* win;
-    Thresh th;           // a pair prunes iff rho_fp32 > rho_prune_of(th)
-    int32_t* work;       // work counter (zeroed before launch)
-    unsigned long long* pairs;  // evaluated pairs
-    unsigned long long* seeds;  // direct dot products computed (top-row / first-column)
-    // select
-    uint32_t* bits;      // candidate bitmap
-    int64_t cap;         // columns scanned per strip beyond its triangle
-    // refine
-    const int32_t* strips;  // strips (of 32*D rows) to sweep
-    const int32_t* nref;    // number of strips (device)
-    int32_t seg;         // columns per work item (multiple of 256)
-    const int32_t* slot_of; // window -> survivor slot of this batch, -1 otherwise
-    int32_t* dead;       // [slots]
-    uint32_t* gmax;      // [slots] enc_f32 of the maximum rho
-    float* cmax;         // [slots][nchunks] maximum rho per 32-column chunk
-    int32_t nchunks;
-};
-
-struct CompactArgs {
-    const uint32_t* bits;
-    int64_t N;
-    int32_t* surv;       // out: ascending survivor indices
-    int32_t* nsurv;      // out: count
-};
-
-struct RefineArgs {
-    const int32_t* list;   // survivor slots handled by the direct form
-    const int32_t* nlist;  // their number (device)
-    const float* T;
-    int64_t n;
-    int64_t N;
-    int32_t m;
-    int32_t kpad;        // m rounded up to the K chunk
-    const WinRec* win;
-    const int32_t* surv; // survivor indices of this batch
-    int32_t ns;          // survivors in this batch
-    const float* acen;   // [ns][kpad] centred survivor windows (FP32)
-    const float* asum;   // [ns] sum of acen row
-    Thresh th;           // mark dead iff rho_fp32 > rho_prune_of(th)
-    int32_t nchunks;     // 32-column chunks
-    uint32_t* gmax;      // [ns] enc_f32 of max rho
-    int32_t* dead;       // [ns]
-    float* cmax;         // [ns][nchunks] maximum rho per 32-column chunk
-    const int32_t* flags;
-    int32_t* work;
-    unsigned long long* pairs;
-};
-
-struct RecheckArgs {
-    const float* T;
-    int64_t n;
-    int64_t N;
-    int32_t m;
-    int32_t kpad;
-    const WinRec* win;
-    const double* mu;
-    const double* var;
-    const int32_t* surv;
-    int32_t ns;
-    const float* acen;
-    const uint32_t* gmax;
-    const int32_t* dead;
-    const float* cmax;
-    int32_t nchunks;
-    Thresh th;           // columns with rho_fp32 >= max - 2 eps_bound(th) are re-checked
-    unsigned long long* nn2;   // [ns] FP64 bits of min d^2 (atomicMin)
-    const int32_t* flags;
-    unsigned long long* pairs;
-    unsigned int* maxerr;      // enc of max |rho_fp32 - rho_fp64|
-};
-
-struct GatherArgs {
-    const int32_t* surv;
-    int32_t ns;
-    const int32_t* dead;
-    const unsigned long long* nn2;
-    double r;
-    int32_t* out_idx;    // discord list (appended)
-    double* out_nn;
-    int32_t* count;      // running count (device)
-};
-
-struct TopkArgs {
-    const int32_t* idx;
-    const double* nn;
-    const int32_t* count;
-    int32_t K;
-    int32_t m;
-    int32_t exclusive;
-    int64_t* pick_idx;   // [K]
-    double* pick_nn;     // [K]
-};
-
-struct HeatArgs {
-    const int32_t* idx;
-    const double* nn;
-    const int32_t* count;
-    int32_t m;
-    float* row;
-};
+// Lane of a global item index given the per-lane prefix `base` (ascending)
+// staged in shared memory: largest l with base[l] <= item.
+__device__ __forceinline__ int lane_of(const int64_t* base, int nl, int64_t item) {
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 // Launchers (each returns the launch's cudaError_t).
-cudaError_t launch_stats_init(const float* T, int64_t n, int32_t m, double* mu, double* var,
-                              int32_t* flags, cudaStream_t s);
-cudaError_t launch_stats_step(const StatsArgs& a, cudaStream_t s);
-cudaError_t launch_select(const SweepArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_refine_sweep(const SweepArgs& a, int grid, cudaStream_t s);
-int sweep_grid(int device);
-cudaError_t launch_plan(const int32_t* surv, int32_t ns, const WinRec* win, int32_t H, int32_t thr, int32_t* slot_of,
-                        int32_t* scount, int32_t* strips, int32_t* nstrips, int32_t* direct, int32_t* ndirect,
-                        cudaStream_t s);
-cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
-cudaError_t launch_refine_prep(const float* T, const WinRec* win, const int32_t* surv, int32_t ns, int32_t m,
-                               int32_t kpad, float* acen, float* asum, cudaStream_t s);
-cudaError_t launch_refine(const RefineArgs& a, int grid, cudaStream_t s);
-int refine_grid(int device);
-cudaError_t launch_recheck(const RecheckArgs& a, cudaStream_t s);
-cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
-cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s);
-cudaError_t launch_heat(const HeatArgs& a, cudaStream_t s);
+cudaError_t launch_stats_init(const float* T, int64_t n, int32_t m, double* mu, double* var, int32_t* flags,
+                              cudaStream_t s);
+cudaError_t launch_stats(const Pass& p, const int32_t* chain_first, int32_t nchains, int64_t nmax, cudaStream_t s);
+cudaError_t launch_select(const Pass& p, int grid, cudaStream_t s);
+cudaError_t launch_compact(const Pass& p, cudaStream_t s);
+cudaError_t launch_plan(const Pass& p, cudaStream_t s);
+cudaError_t launch_refine_sweep(const Pass& p, int grid, cudaStream_t s);
+cudaError_t launch_refine_direct(const Pass& p, int grid, cudaStream_t s);
+cudaError_t launch_recheck(const Pass& p, int grid, cudaStream_t s);
+cudaError_t launch_round_reset(const Pass& p, cudaStream_t s);
+cudaError_t launch_gather(const Pass& p, cudaStream_t s);
+cudaError_t launch_topk(const Pass& p, cudaStream_t s);
+cudaError_t launch_finalize(const Pass& p, cudaStream_t s);
+int sm_count(int device);
 
 }  // namespace palmad

@@ -148,6 +148,20 @@ def test_merlin_matches_oracle(ctx, name, minL, maxL, K, excl):
     _check_merlin(got, want, heat=True)
 
 
+@pytest.mark.parametrize("W", [4, 16])
+@pytest.mark.parametrize("name,minL,maxL,K,excl", [
+    ("rw3000", 10, 40, 3, True),
+    ("sine4000", 40, 75, 2, True),
+    ("flat2200", 20, 45, 2, False),
+])
+def test_merlin_batched_matches_oracle(ctx, W, name, minL, maxL, K, excl):
+    """Batched form: W lengths per pass at a speculative r, exact replay."""
+    T = SERIES[name]()
+    got = ctx.palmad_find_discords(T, minL, maxL, K, _opts(exclusive_topk=int(excl), batch_lengths=W), heatmap=True)
+    want = oracle.merlin(T, minL, maxL, K, excl, heatmap=True)
+    _check_merlin(got, want, heat=True)
+
+
 def test_merlin_options_do_not_change_results(ctx):
     T = SERIES["rw3000"]()
     base = ctx.palmad_find_discords(T, 12, 20, 2)
@@ -166,12 +180,13 @@ def test_device_entry_equals_host_entry(ctx):
     np.testing.assert_array_equal(dev["r"].cpu().numpy(), host["r"])
 
 
-def test_batch_entry_equals_single_calls(ctx):
-    series = [SERIES["rw3000"](), SERIES["sine4000"](), synth.random_walk(1800, 47)]
-    mins, maxs = [10, 40, 30], [14, 44, 33]
-    outs = ctx.palmad_find_discords_batch(series, mins, maxs, 1)
+@pytest.mark.parametrize("W", [0, 8])
+def test_batch_entry_equals_oracle(ctx, W):
+    series = [SERIES["rw3000"](), SERIES["sine4000"](), synth.random_walk(1800, 47), synth.random_walk(2500, 49)]
+    mins, maxs = [10, 40, 30, 12], [24, 58, 33, 40]
+    outs = ctx.palmad_find_discords_batch(series, mins, maxs, 2, _opts(batch_lengths=W))
     for T, a, b, o in zip(series, mins, maxs, outs):
-        want = oracle.merlin(T, a, b, 1, True)
+        want = oracle.merlin(T, a, b, 2, True)
         _check_merlin(o, want)
 
 
@@ -230,6 +245,14 @@ def test_full_size_schedule_closed_forms(sine100k):
             k = (mu - 2 * sd - r[l]) / sd
             assert abs(k - round(k)) < 1e-6 and round(k) >= 0
         assert res["nn"][l, K - 1] >= r[l]
+
+
+def test_full_size_batched_equals_plain(ctx, sine100k):
+    """The batched form returns exactly the plain form's results."""
+    w, T, plain = sine100k
+    got = ctx.palmad_find_discords(T, w.minL[0], w.maxL[0], w.topK, _opts(batch_lengths=16), heatmap=True)
+    for k in ("idx", "nn", "count", "r", "heatmap"):
+        np.testing.assert_array_equal(got[k], plain[k])
 
 
 def test_full_size_sampled_against_brute_force(sine100k):
