@@ -91,7 +91,10 @@ typedef struct {
     int32_t use_graph;       /* 1: capture the batched form's launches in a CUDA graph */
     int32_t profile;         /* 1: time every kernel launch with CUDA events
                                 (palmad_get_stats) */
-    int32_t reserved[5];
+    int32_t pool_slots;      /* cap on the survivors refined at once (0 = as many as
+                                about 1 GiB of per-survivor buffers holds); more
+                                survivors are refined in several rounds */
+    int32_t reserved[4];
 } palmad_options;
 
 /* Per-call counters of the most recent find/drag call. */

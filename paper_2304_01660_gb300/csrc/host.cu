@@ -233,6 +233,7 @@ palmad_status read_options(palmad_ctx* ctx, const palmad_options* in, palmad_opt
         return fail(ctx, PALMAD_ERR_ARG, "unknown precision");
     if (o.select_cap < 0) return fail(ctx, PALMAD_ERR_ARG, "select_cap must be >= 0");
     if (o.batch_lengths < 0 || o.batch_lengths > 1024) return fail(ctx, PALMAD_ERR_ARG, "batch_lengths must lie in [0, 1024]");
+    if (o.pool_slots < 0) return fail(ctx, PALMAD_ERR_ARG, "pool_slots must be >= 0");
     return PALMAD_OK;
 }
 
@@ -385,14 +386,17 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     ctx->stats.device_passes += 1;
 
     // Refine rounds: lanes' survivors in order, as many as the pool holds.
+    const int32_t pool = o.pool_slots > 0 ? std::min(ctx->pool, std::max(64, (o.pool_slots + 63) / 64 * 64)) : ctx->pool;
     std::vector<int32_t> done(nl, 0);
-    for (;;) {
+    for (int round = 0;; ++round) {
+        // the pinned lane mirror still feeds the previous round's upload
+        if (round > 0) CK(cudaStreamSynchronize(ctx->stream));
         int32_t used = 0;
         bool any = false;
         for (int l = 0; l < nl; ++l) {
             Lane& L = ctx->h_lanes[l];
             const int32_t rem = ctx->h_st[l].nsurv - done[l];
-            const int32_t room = ctx->pool - used;
+            const int32_t room = pool - used;
             const int32_t take = std::max(0, std::min(rem, room));
             L.k_lo = done[l];
             L.k_hi = done[l] + take;
@@ -402,7 +406,7 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
                 used += ((take + 63) / 64) * 64;
                 done[l] += take;
             }
-            if (used >= ctx->pool) used = ctx->pool;
+            if (used >= pool) used = pool;
         }
         if (!any) break;
         p.nslots = used;
@@ -553,6 +557,7 @@ struct SeriesJob {
     std::vector<std::vector<double>> wnn;
     int32_t rerun_l = -1;       // length awaiting a rerun result
     double rerun_r = 0.0;
+    std::vector<double> first_r;  // first try of each length (for the deficit)
 
     int set_of(int32_t li) const { return set0 + (W > 1 ? (li % W) : 0); }
     int32_t m_of(int32_t li) const { return minL + li; }
@@ -595,20 +600,30 @@ Lane make_lane(palmad_ctx* ctx, SeriesJob& s, int32_t li, double r, const palmad
     return L;
 }
 
+// How far below its first try the schedule ended, recently (largest of the
+// last eight decided lengths).
+double recent_deficit(const SeriesJob& s, int32_t l0) {
+    double d = 0.0;
+    for (int32_t q = std::max(5, l0 - 8); q < l0; ++q) d = std::max(d, s.first_r[q] - s.r_final[q]);
+    return d;
+}
+
 // Speculative threshold for the window lengths: below the first try of the
-// schedule with room for about two decrements.
+// schedule by about two decrements, 6%, or 1.5x the recent deficit,
+// whichever is largest (never below half the recent mean).
 double speculative_r(const SeriesJob& s, int32_t l0) {
     double mean = 0.0, var = 0.0;
     for (int q = 1; q <= 5; ++q) mean += s.sched[l0 - q];
     mean /= 5.0;
     for (int q = 1; q <= 5; ++q) var += (s.sched[l0 - q] - mean) * (s.sched[l0 - q] - mean);
     const double sdv = std::sqrt(var / 4.0);
-    const double r = mean - 2.0 * sdv - 2.0 * std::max(sdv, 0.03 * mean);
-    return std::max(r, 0.5 * mean);
+    const double margin = std::max({2.0 * sdv, 0.06 * mean, 1.5 * recent_deficit(s, l0)});
+    return std::max(mean - 2.0 * sdv - margin, 0.5 * mean);
 }
 
 void accept_length(SeriesJob& s, int32_t li, double r, const LaneState& st, const int64_t* pidx, const double* pnn,
                    std::vector<PassLane>& fin, palmad_ctx* ctx, const palmad_options& o) {
+    (void)ctx;
     int got = 0;
     for (int q = 0; q < s.K; ++q) {
         const bool ok = pidx[q] >= 0 && (r <= 0.0 || pnn[q] >= r);
@@ -655,6 +670,7 @@ void series_request(palmad_ctx* ctx, SeriesJob& s, std::vector<PassLane>& req, s
     if (!s.tr_started) {
         s.tr.start(s.l, s.sched, s.minL);
         s.tr_started = true;
+        s.first_r[s.l] = s.tr.r;
     }
     push(s.l, s.tr.r, false);
     s.phase = SeriesJob::kPlain;
@@ -669,16 +685,20 @@ void series_replay(palmad_ctx* ctx, SeriesJob& s, std::vector<PassLane>& fin, co
         if (!s.tr_started) {
             s.tr.start(s.l, s.sched, s.minL);
             s.tr_started = true;
+            s.first_r[s.l] = s.tr.r;
         }
         const double rs = s.rspec[w];
         for (;;) {
             const double r = s.tr.r;
             if (!(rs <= 0.0 || r >= rs)) {
-                // the schedule needs r below this length's r': rerun it lower
+                // the schedule needs r below this length's r': rerun it lower,
+                // by at least three decrements, 10% or 1.5x the recent deficit
                 const double step = s.tr.step > 0.0 ? s.tr.step : 0.01 * r;
+                const double drop = std::max({3.0 * step, 0.1 * r, 1.5 * recent_deficit(s, s.l)});
                 s.rerun_l = s.l;
-                s.rerun_r = std::max(0.0, r - 3.0 * step);
-                if (s.rerun_r < 1e-9 * r) s.rerun_r = 0.0;
+                s.rerun_r = r - drop;
+                if (s.rerun_r < 0.05 * r) s.rerun_r = 0.05 * r;  // stay clear of the r = 0 full profile
+                if (r <= 0.0) s.rerun_r = 0.0;
                 s.phase = SeriesJob::kRerun;
                 ctx->stats.reruns += 1;
                 return;
@@ -762,6 +782,7 @@ palmad_status run_jobs(palmad_ctx* ctx, std::vector<SeriesJob>& jobs, const palm
         s.r_final.assign(s.L, 0.0);
         s.sched.assign(s.L, 0.0);
         s.lstate.assign(s.L, LaneState{});
+        s.first_r.assign(s.L, 0.0);
     }
     // initial statistics (Eq. 4 at minL) and the non-finite check
     CKS(ensure(ctx, ctx->init_flags, jobs.size()));

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
         ("select_cap", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
         ("profile", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("pool_slots", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 

@@ -162,6 +162,21 @@ def test_merlin_batched_matches_oracle(ctx, W, name, minL, maxL, K, excl):
     _check_merlin(got, want, heat=True)
 
 
+@pytest.mark.parametrize("W", [0, 8])
+def test_refine_rounds_match_oracle(ctx, W):
+    """A tiny survivor pool forces many refine rounds per pass (lanes split
+    across rounds, strips split across rounds)."""
+    series = [SERIES["rw3000"](), SERIES["sine4000"](), synth.random_walk(2600, 50)]
+    mins, maxs = [10, 40, 14], [30, 60, 36]
+    outs = ctx.palmad_find_discords_batch(series, mins, maxs, 2, _opts(batch_lengths=W, pool_slots=64))
+    for T, a, b, o in zip(series, mins, maxs, outs):
+        _check_merlin(o, oracle.merlin(T, a, b, 2, True))
+    T = SERIES["rw3000"]()
+    mp, _ = oracle.matrix_profile(T, 25)
+    r = float(_thresholds(mp, (0.3,))[0])
+    _check_drag(ctx, T, 25, r, _opts(pool_slots=100))
+
+
 def test_merlin_options_do_not_change_results(ctx):
     T = SERIES["rw3000"]()
     base = ctx.palmad_find_discords(T, 12, 20, 2)
