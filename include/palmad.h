@@ -64,7 +64,8 @@ typedef enum {
     PALMAD_ERR_CUDA = -4,        /* a CUDA runtime call or kernel failed */
     PALMAD_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
     PALMAD_ERR_UNSUPPORTED = -6, /* option or size not supported by this build */
-    PALMAD_ERR_INTERNAL = -7     /* an internal consistency check failed */
+    PALMAD_ERR_INTERNAL = -7,    /* an internal consistency check failed */
+    PALMAD_ERR_TOO_LARGE = -8    /* size beyond the fixed scratch of palmad_topk_profile_noalloc */
 } palmad_status;
 
 /* Arithmetic of the pair evaluations (the candidate-select and refine dot
@@ -205,6 +206,38 @@ palmad_status palmad_find_discords_batch(palmad_ctx *ctx, int32_t count, const f
  */
 palmad_status palmad_drag(palmad_ctx *ctx, const float *T, int64_t n, int32_t m, double r, const palmad_options *opt,
                           int64_t *out_idx, double *out_nndist, int64_t cap, int64_t *out_count);
+
+/*
+ * Greedy top-K range discords of a nearest-neighbour profile the caller
+ * already holds, WITHOUT ANY ALLOCATION.  The paper has no counterpart: it is
+ * for callers that cannot call cudaMalloc, such as code running while
+ * another component owns all device memory through its own allocator, or a
+ * latency-critical path that cannot afford cudaMalloc's implicit device
+ * synchronisation.  It needs no context.
+ *   nn_dev         [N] FP64 nearest-neighbour distances (device); +inf or NaN
+ *                  marks a window without a nearest neighbour.
+ *   N              1 <= N <= PALMAD_NOALLOC_MAX_WINDOWS; larger N returns
+ *                  PALMAD_ERR_TOO_LARGE.
+ *   m, r, K        window length (for the exclusion zone), threshold and
+ *                  1 <= K <= 1024.  Range discords: finite entries >= r (every
+ *                  finite entry when r <= 0), picked as in
+ *                  palmad_find_discords (distance desc, index asc; with
+ *                  exclusive != 0 each pick >= m from earlier picks).
+ *   out_idx_dev    [K] int64 picks, -1 past the last one (device).
+ *   out_nn_dev     [K] double, their distances, 0.0 past the last one (device).
+ *   out_count_dev  [1] int64 number of range discords (device) or NULL.
+ *   cuda_stream    stream to run on (NULL: the default stream).
+ * The call is asynchronous: results are ready once the stream reaches them.
+ * Its one intermediate buffer is a fixed device array of the library
+ * (PALMAD_NOALLOC_MAX_WINDOWS x 12 bytes per GPU, resident until the process
+ * exits).  The first call on each device looks up that array's address with
+ * cudaGetSymbolAddress, so make it before any stream capture.  All calls on
+ * a device share the array: calls whose kernels overlap on the GPU race.
+ */
+#define PALMAD_NOALLOC_MAX_WINDOWS (1 << 18)
+palmad_status palmad_topk_profile_noalloc(const double *nn_dev, int64_t N, int32_t m, double r, int32_t K,
+                                          int32_t exclusive, int64_t *out_idx_dev, double *out_nn_dev,
+                                          int64_t *out_count_dev, void *cuda_stream);
 
 /* Counters of the most recent find/drag call on this context. */
 palmad_status palmad_get_stats(const palmad_ctx *ctx, palmad_stats *out);

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libpalmad.so")
 
 PALMAD_OK = 0
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NONFINITE", -3: "ERR_OOM", -4: "ERR_CUDA", -5: "ERR_TIMEOUT",
-          -6: "ERR_UNSUPPORTED", -7: "ERR_INTERNAL"}
+          -6: "ERR_UNSUPPORTED", -7: "ERR_INTERNAL", -8: "ERR_TOO_LARGE"}
+NOALLOC_MAX_WINDOWS = 1 << 18
 PREC_FP32, PREC_MIXED = 0, 1
 KERNELS = ["stats", "select", "compact", "plan", "refine_sweep", "refine_direct", "recheck", "gather", "topk", "heat",
            "other", "spare"]
@@ -100,8 +101,11 @@ def load(path: str = LIB_PATH):
                                                ctypes.POINTER(Options), _vp, _vp, _vp, _vp]
     lib.palmad_drag.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                 ctypes.POINTER(Options), _vp, _vp, ctypes.c_int64, _i64p]
+    lib.palmad_topk_profile_noalloc.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                                ctypes.c_int32, _vp, _vp, _vp, _vp]
     for name in ("palmad_default_options", "palmad_create", "palmad_get_stats", "palmad_find_discords",
-                 "palmad_find_discords_device", "palmad_find_discords_batch", "palmad_drag"):
+                 "palmad_find_discords_device", "palmad_find_discords_batch", "palmad_drag",
+                 "palmad_topk_profile_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -119,6 +123,25 @@ def palmad_default_options(**kw) -> Options:
             raise KeyError(k)
         setattr(o, k, v)
     return o
+
+
+def palmad_topk_profile_noalloc(nn_dev, m: int, r: float, K: int, exclusive: bool = True, stream=None):
+    """Top-K range discords of a device profile (float64 CUDA tensor) with no
+    allocation inside the library; the output tensors are allocated here by
+    torch, on the caller's side.  Returns (idx, nn, count) CUDA tensors,
+    ready once `stream` (default: torch's current stream) reaches them."""
+    import torch
+    assert nn_dev.is_cuda and nn_dev.dtype == torch.float64 and nn_dev.is_contiguous()
+    dev = nn_dev.device
+    idx = torch.empty(K, dtype=torch.int64, device=dev)
+    nn = torch.empty(K, dtype=torch.float64, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    st = load().palmad_topk_profile_noalloc(nn_dev.data_ptr(), nn_dev.numel(), m, float(r), K, int(bool(exclusive)),
+                                            idx.data_ptr(), nn.data_ptr(), cnt.data_ptr(), s)
+    if st != PALMAD_OK:
+        raise PalmadError(st, "palmad_topk_profile_noalloc failed")
+    return idx, nn, cnt
 
 
 def _ptr(a) -> int:
