@@ -186,7 +186,8 @@ def run_ours(args, w):
     prof = 0 if args.no_events else 1
     forms = {"plain": palmad.palmad_default_options(profile=prof),
              "batched": palmad.palmad_default_options(profile=prof, batch_lengths=args.batch)}
-    best = args.form
+    forms = {f: o for f, o in forms.items() if f in args.forms.split(",")}
+    best = args.form if args.form in forms else next(iter(forms))
 
     def step(form):
         return ctx.palmad_find_discords_device(T_dev, minL, maxL, K, forms[form])
@@ -324,6 +325,7 @@ def main(argv=None):
     ap.add_argument("--no-events", action="store_true", help="no per-launch CUDA events (profiler runs)")
     ap.add_argument("--form", choices=["plain", "batched"], default="batched", help="form reported as `value`")
     ap.add_argument("--batch", type=int, default=16, help="lengths per pass of the batched form")
+    ap.add_argument("--forms", default="plain,batched", help="forms to time (comma separated)")
     args = ap.parse_args(argv)
     w = synth.workload(args.workload)
     if args.impl == "reference":

@@ -185,7 +185,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const Pass p) {
         __syncthreads();
     }
     const int64_t nseg = REFINE ? (p.nmax + p.seg - 1) / p.seg : 1;
-    const int64_t nitems = REFINE ? int64_t(*p.nref) * nseg : p.sel_items;
+    const int64_t nref = REFINE ? int64_t(*p.nref) : 0;
+    // refine items: rank k (0, +1, -1, +2, -2, ... segments away from the
+    // strip's own segment) major, strip minor -- the segments nearest every
+    // strip run first, so survivors pruned there skip the far ones
+    const int64_t nitems = REFINE ? nref * 2 * nseg : p.sel_items;
     unsigned long long pairs = 0, seeds = 0;
 
     for (;;) {
@@ -195,10 +199,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const Pass p) {
         if (item >= nitems) break;
         int l;
         int64_t s;
+        int64_t kq = 0;
         if (REFINE) {
-            const int2 e = p.strips[item / nseg];
+            const int2 e = p.strips[item % nref];
             l = e.x;
             s = e.y;
+            kq = item / nref;
         } else {
             l = lane_of(strip_base, p.nl, item);
             s = item - strip_base[l];
@@ -211,8 +217,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const Pass p) {
         const float rho_prune = rho_prune_of(Lg, p.st[l]);
         int64_t ja, jb;
         if (REFINE) {
-            ja = (item % nseg) * p.seg;
-            if (ja >= N) continue;
+            const int64_t q0 = (s * H + H / 2) / p.seg;
+            const int64_t d = (kq + 1) / 2;
+            const int64_t q = (kq & 1) ? q0 + d : q0 - d;
+            ja = q * p.seg;
+            if (q < 0 || ja >= N) continue;
             jb = min64(N, ja + p.seg);
         } else {
             ja = s * H + m;
