@@ -1,0 +1,87 @@
+"""Multi-process (one process per GPU) host logic.
+
+Discord discovery shards in two ways:
+
+* independent series (the batched multi-series entry) split across ranks
+  with no data-path collective -- each rank runs MERLIN on its own series
+  (weak scaling);
+* one long series could split its pair space across ranks, with one
+  exchange per DRAG phase: a bitwise AND of the candidate bitmaps after
+  select (a window pruned by any rank is pruned) and an elementwise minimum
+  of the survivors' nearest-neighbour distances after refine (each rank saw
+  a slice of the columns).  These are the exchange steps of the cluster DRAG
+  the paper cites as related work (Sec. 1); the primitives below implement
+  them on torch.distributed, and the tests run them on CPU ranks.
+
+Timing across ranks follows the benchmark contract: the job time is the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import heapq
+
+import torch
+import torch.distributed as dist
+
+
+def shard_balanced(weights, rank: int, world: int) -> list[int]:
+    """Indices of the items rank `rank` owns, by longest-processing-time
+    greedy assignment of `weights` (e.g. points x lengths per series) to
+    `world` ranks.  Deterministic: every rank computes the same split."""
+    order = sorted(range(len(weights)), key=lambda i: (-weights[i], i))
+    heap = [(0.0, r) for r in range(world)]
+    heapq.heapify(heap)
+    owner = [0] * len(weights)
+    for i in order:
+        load, r = heapq.heappop(heap)
+        owner[i] = r
+        heapq.heappush(heap, (load + float(weights[i]), r))
+    return [i for i in range(len(weights)) if owner[i] == rank]
+
+
+def max_over_ranks(value: float, device="cpu") -> float:
+    """Maximum of a per-rank scalar (the job time of a timed region)."""
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, device="cpu") -> float:
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def candidate_and_(bits: torch.Tensor) -> torch.Tensor:
+    """In place: bitwise AND of every rank's packed candidate bitmap (int32
+    words; bit i of word w is window 32w+i)."""
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(bits, op=dist.ReduceOp.BAND)
+    return bits
+
+
+def nn_min_(nn: torch.Tensor) -> torch.Tensor:
+    """In place: elementwise minimum of every rank's nearest-neighbour
+    distances (float64; +inf where a rank saw no non-self match)."""
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(nn, op=dist.ReduceOp.MIN)
+    return nn
+
+
+def column_slice(N: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous column range [lo, hi) of rank `rank` when the columns of
+    the distance matrix are split evenly across `world` ranks."""
+    per = (N + world - 1) // world
+    lo = min(N, rank * per)
+    return lo, min(N, lo + per)
+
+
+def gather_objects(obj, world: int) -> list:
+    """All ranks' Python objects, in rank order (results of owned series)."""
+    if world <= 1:
+        return [obj]
+    out = [None] * world
+    dist.all_gather_object(out, obj)
+    return out
