@@ -291,7 +291,8 @@ def run_ours(args, w):
             "gpu_launches": launches,
             "roofline": roof,
             "clocks": clk.summary(),
-            "kernel_ms_per_step": {k2: v / args.steps for k2, v in kernel_ms.items()},
+            "kernel_ms_per_step": {k2: v / args.steps for k2, v in kernel_ms.items() if v},
+            "kernel_tflops": {k2: flops[k2] / (kernel_ms[k2] / 1e3) / 1e12 for k2 in flops if kernel_ms.get(k2, 0) > 0},
             "pairs_per_step": {k2: v / args.steps for k2, v in pairs.items()},
             "launches_per_step": launches_per,
             "drag_calls_per_step": last_stats["drag_calls"],

@@ -283,9 +283,21 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
 
 __device__ __forceinline__ bool is_flat64(double mu, double sd) { return sd <= kFlatRel * fabs(mu); }
 
+// One CTA per live survivor slot (persistent): threads recompute the FP32
+// rho of every column in a flagged 32-column chunk; the columns within 2 eps
+// of the FP32 maximum go to a shared candidate list, and each warp then
+// evaluates one candidate's FP64 distance with the m terms split over its
+// lanes (the survivor's z-normalised FP64 window is staged once in shared
+// memory).
+constexpr int kRecheckCand = 512;
+constexpr int kRecheckWin = 1024;   // survivor windows up to this length use shared memory
+
 __global__ void __launch_bounds__(256) k_recheck(const Pass p) {
     __shared__ int32_t flagged[256];
-    __shared__ int nflag;
+    __shared__ int32_t cand[kRecheckCand];
+    __shared__ float candr[kRecheckCand];
+    __shared__ double zc[kRecheckWin];
+    __shared__ int nflag, ncand;
     __shared__ int64_t g_s;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long fp64 = 0;
@@ -310,6 +322,10 @@ __global__ void __launch_bounds__(256) k_recheck(const Pass p) {
         const float invc = win[c].z;
         const double muc = L.mu[c], sdc = sqrt(L.var[c]);
         const bool flatc = is_flat64(muc, sdc);
+        const double ic = flatc ? 0.0 : 1.0 / sdc;
+        const bool zc_smem = m <= kRecheckWin;
+        if (zc_smem)
+            for (int k = threadIdx.x; k < m; k += blockDim.x) zc[k] = (double(T[c + k]) - muc) * ic;
         const float* arow = p.acen + g * int64_t(p.kpad_max);
         const float* cm = p.cmax + g * int64_t(p.nchunks_max);
         const int32_t nchunks = int32_t((N + 31) / 32);
@@ -320,34 +336,53 @@ __global__ void __launch_bounds__(256) k_recheck(const Pass p) {
             if (q < nchunks && cm[q] >= thr) flagged[atomicAdd(&nflag, 1)] = q;
             __syncthreads();
             const int nf = nflag;
-            for (int f = wid; f < nf; f += 8) {
-                const int64_t j = int64_t(flagged[f]) * 32 + lane;
-                if (j >= N || (j - c < m && c - j < m)) continue;
-                const float4 rj = win[j];
-                float acc = 0.f;
-                for (int k = 0; k < m; ++k) acc = fmaf(arow[k], T[j + k] - rj.w, acc);
-                float rho32 = acc * invc * rj.z;
-                if (has_flat && (invc == 0.f || rj.z == 0.f)) rho32 = (invc == 0.f && rj.z == 0.f) ? 1.f : 0.f;
-                if (rho32 < thr) continue;
-                const double muj = L.mu[j], sdj = sqrt(L.var[j]);
-                const bool flatj = is_flat64(muj, sdj);
-                double d2;
-                if (flatc && flatj) d2 = 0.0;
-                else if (flatc || flatj) d2 = 2.0 * m;
-                else {
-                    d2 = 0.0;
-                    const double ic = 1.0 / sdc, ij = 1.0 / sdj;
-                    for (int k = 0; k < m; ++k) {
-                        const double x = (double(T[c + k]) - muc) * ic - (double(T[j + k]) - muj) * ij;
-                        d2 = fma(x, x, d2);
+            // flagged chunks 8 at a time (one per warp), candidates per batch
+            for (int f0 = 0; f0 < nf; f0 += 8) {
+                if (threadIdx.x == 0) ncand = 0;
+                __syncthreads();
+                const int f = f0 + wid;
+                if (f < nf) {
+                    const int64_t j = int64_t(flagged[f]) * 32 + lane;
+                    if (j < N && (j - c >= m || c - j >= m)) {
+                        const float4 rj = win[j];
+                        float acc = 0.f;
+                        for (int k = 0; k < m; ++k) acc = fmaf(arow[k], T[j + k] - rj.w, acc);
+                        float rho32 = acc * invc * rj.z;
+                        if (has_flat && (invc == 0.f || rj.z == 0.f)) rho32 = (invc == 0.f && rj.z == 0.f) ? 1.f : 0.f;
+                        if (rho32 >= thr) {
+                            const int at = atomicAdd(&ncand, 1);  // <= 256 per batch
+                            cand[at] = int32_t(j);
+                            candr[at] = rho32;
+                        }
                     }
                 }
-                atomicMin(&p.nn2[g], static_cast<unsigned long long>(__double_as_longlong(d2)));
-                const float err = fabsf(rho32 - float(1.0 - d2 / (2.0 * m)));
-                atomicMax(&S.maxerr, enc_f32(err));
-                ++fp64;
+                __syncthreads();
+                const int nc = ncand;
+                for (int e = wid; e < nc; e += 8) {
+                    const int64_t j = cand[e];
+                    const double muj = L.mu[j], sdj = sqrt(L.var[j]);
+                    const bool flatj = is_flat64(muj, sdj);
+                    double d2 = 0.0;
+                    if (flatc && flatj) d2 = 0.0;
+                    else if (flatc || flatj) d2 = 2.0 * m;
+                    else {
+                        const double ij = 1.0 / sdj;
+                        for (int k = lane; k < m; k += 32) {
+                            const double zck = zc_smem ? zc[k] : (double(T[c + k]) - muc) * ic;
+                            const double x = zck - (double(T[j + k]) - muj) * ij;
+                            d2 = fma(x, x, d2);
+                        }
+#pragma unroll
+                        for (int o = 16; o >= 1; o >>= 1) d2 += __shfl_xor_sync(kFull, d2, o);
+                    }
+                    if (lane == 0) {
+                        atomicMin(&p.nn2[g], static_cast<unsigned long long>(__double_as_longlong(d2)));
+                        atomicMax(&S.maxerr, enc_f32(fabsf(candr[e] - float(1.0 - d2 / (2.0 * m)))));
+                        ++fp64;
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
     if (fp64) atomicAdd(p.pairs + 2, fp64);
