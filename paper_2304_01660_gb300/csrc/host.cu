@@ -93,7 +93,8 @@ struct palmad_ctx {
     // refine pool
     int32_t pool = 0;
     int32_t pool_kpad = 0, pool_nchunks = 0;
-    DBuf<int32_t> slot_lane, slot_win, route, dead;
+    DBuf<int32_t> slot_lane, slot_win, route, dlist, dead;
+    bool sets_dirty = false;       // a pass stopped early: slot maps may not be clean
     DBuf<float> acen, asum, cmax;
     DBuf<uint32_t> gmax;
     DBuf<unsigned long long> nn2;
@@ -157,6 +158,14 @@ void release_set(LaneSet& s) {
     s.cap = 0;
 }
 
+// slot_of stays -1 and scount 0 between refine rounds (each round undoes
+// its own entries); a fresh or reset set starts that way.
+palmad_status clear_maps(palmad_ctx* ctx, LaneSet& s) {
+    CK(cudaMemsetAsync(s.slot_of.p, 0xff, s.slot_of.n * sizeof(int32_t), ctx->stream));
+    CK(cudaMemsetAsync(s.scount.p, 0, s.scount.n * sizeof(int32_t), ctx->stream));
+    return PALMAD_OK;
+}
+
 palmad_status ensure_set(palmad_ctx* ctx, LaneSet& s, int64_t N) {
     if (s.cap >= N) return PALMAD_OK;
     const int64_t P = (N + 31) / 32, S = (N + kStripH - 1) / kStripH + 1;
@@ -164,6 +173,7 @@ palmad_status ensure_set(palmad_ctx* ctx, LaneSet& s, int64_t N) {
     CKS(ensure(ctx, s.bits0, P)); CKS(ensure(ctx, s.bits, P));
     CKS(ensure(ctx, s.surv, N)); CKS(ensure(ctx, s.slot_of, N)); CKS(ensure(ctx, s.scount, S));
     CKS(ensure(ctx, s.didx, N)); CKS(ensure(ctx, s.dnn, N));
+    CKS(clear_maps(ctx, s));
     s.cap = N;
     return PALMAD_OK;
 }
@@ -299,6 +309,7 @@ palmad_status ensure_pool(palmad_ctx* ctx, int32_t kpad, int32_t nchunks) {
     slots = std::min<int64_t>(slots, 1 << 17);
     slots = std::max<int64_t>(64, (slots / 64) * 64);
     CKS(ensure(ctx, ctx->slot_lane, slots)); CKS(ensure(ctx, ctx->slot_win, slots)); CKS(ensure(ctx, ctx->route, slots));
+    CKS(ensure(ctx, ctx->dlist, slots));
     CKS(ensure(ctx, ctx->dead, slots)); CKS(ensure(ctx, ctx->asum, slots)); CKS(ensure(ctx, ctx->gmax, slots));
     CKS(ensure(ctx, ctx->nn2, slots));
     CKS(ensure(ctx, ctx->acen, size_t(slots) * kpad));
@@ -322,6 +333,7 @@ Pass base_pass(palmad_ctx* ctx, int nl, int K, bool exclusive, const palmad_opti
     p.slot_lane = ctx->slot_lane.p;
     p.slot_win = ctx->slot_win.p;
     p.route = ctx->route.p;
+    p.dlist = ctx->dlist.p;
     p.acen = ctx->acen.p;
     p.asum = ctx->asum.p;
     p.gmax = ctx->gmax.p;
@@ -362,11 +374,12 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
         if (l == 0 || !req[l - 1].lane.chain_next) ctx->h_chain[nchains++] = l;
         ctx->h_lanes[l] = L;
         LaneState s = req[l].state;
-        s.nsurv = 0; s.dcount = 0; s.got = 0; s.count_final = 0; s.maxerr = 0;
+        s.nsurv = 0; s.dcount = 0; s.got = 0; s.count_final = 0; s.maxerr = 0; s.ndirect = 0;
         if (L.stats_mode != 0) { s.flags = 0; s.ab[0] = 0; s.ab[1] = 0; }
         ctx->h_st[l] = s;
     }
     CKS(ensure_pool(ctx, kpad_max, nchunks_max));
+    ctx->sets_dirty = true;
     Pass p = base_pass(ctx, nl, K, exclusive, o);
     p.sel_items = strips;
     p.nmax = nmax;
@@ -413,12 +426,12 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
         CK(cudaMemcpyAsync(ctx->lanes.p, ctx->h_lanes, sizeof(Lane) * nl, cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemsetAsync(&ctx->small.p->work[1], 0, 4 * sizeof(int32_t), ctx->stream));
         CK(cudaMemsetAsync(&ctx->small.p->nref, 0, sizeof(int32_t), ctx->stream));
-        LAUNCH(PALMAD_K_PLAN, launch_round_reset(p, ctx->stream));
         LAUNCH(PALMAD_K_PLAN, launch_plan(p, ctx->stream));
         LAUNCH(PALMAD_K_REFINE_SWEEP, launch_refine_sweep(p, ctx->sms * 4, ctx->stream));
         LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_direct(p, ctx->sms * 2, ctx->stream));
         LAUNCH(PALMAD_K_RECHECK, launch_recheck(p, ctx->sms * 8, ctx->stream));
         LAUNCH(PALMAD_K_GATHER, launch_gather(p, ctx->stream));
+        LAUNCH(PALMAD_K_PLAN, launch_round_cleanup(p, ctx->stream));
         bool more = false;
         for (int l = 0; l < nl; ++l) more |= done[l] < ctx->h_st[l].nsurv;
         if (!more) break;
@@ -429,6 +442,7 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     CK(cudaMemcpyAsync(ctx->h_pnn, ctx->pnn.p, sizeof(double) * nl * K, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_small, ctx->small.p, sizeof(Small), cudaMemcpyDeviceToHost, ctx->stream));
     CKS(sync(ctx));
+    ctx->sets_dirty = false;
     out.st.assign(ctx->h_st, ctx->h_st + nl);
     out.idx.assign(ctx->h_pidx, ctx->h_pidx + int64_t(nl) * K);
     out.nn.assign(ctx->h_pnn, ctx->h_pnn + int64_t(nl) * K);
@@ -847,6 +861,11 @@ palmad_status begin_call(palmad_ctx* ctx, const palmad_options& o) {
     reset_stats(ctx);
     ctx->profile = o.profile != 0;
     CK(cudaSetDevice(ctx->device));
+    if (ctx->sets_dirty) {  // an earlier call stopped inside a pass
+        for (LaneSet& s : ctx->sets)
+            if (s.cap > 0) CKS(clear_maps(ctx, s));
+        ctx->sets_dirty = false;
+    }
     return PALMAD_OK;
 }
 
@@ -926,7 +945,7 @@ void palmad_destroy(palmad_ctx* ctx) {
     for (LaneSet& s : ctx->sets) release_set(s);
     release(ctx->lanes); release(ctx->st); release(ctx->chain); release(ctx->small);
     release(ctx->pidx); release(ctx->pnn);
-    release(ctx->slot_lane); release(ctx->slot_win); release(ctx->route); release(ctx->dead);
+    release(ctx->slot_lane); release(ctx->slot_win); release(ctx->route); release(ctx->dlist); release(ctx->dead);
     release(ctx->acen); release(ctx->asum); release(ctx->cmax); release(ctx->gmax); release(ctx->nn2);
     release(ctx->strips); release(ctx->init_flags);
     if (ctx->h_lanes) cudaFreeHost(ctx->h_lanes);

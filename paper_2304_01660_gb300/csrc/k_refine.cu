@@ -9,7 +9,8 @@
 //                 recurrence sweep (k_sweep.cu), else its survivors -> the
 //                 direct form below.
 //  k_prep         centred FP32 window of every slot and its sum.
-//  k_refine       direct FP32 form for scattered survivors: a register-tiled
+//  k_refine       direct FP32 form for scattered survivors (packed per lane,
+//                 64 per group): a register-tiled
 //                 product of 64 survivors' windows with the Hankel matrix of
 //                 the series (256 columns per CTA tile, 8x8 per thread, one new
 //                 series value per k step thanks to the Hankel structure).
@@ -119,7 +120,12 @@ __global__ void k_plan_split(const Pass p) {
         const int32_t len = c & ((1 << 30) - 1);
         const int32_t thr = max(2, (5 * kStripH + 2 * L.m - 1) / L.m);  // sweep when cheaper than direct
         const int sweep = (len >= thr && !(c >> 30)) ? 1 : 0;
-        if (sweep) p.strips[atomicAdd(p.nref, 1)] = make_int2(l, st);
+        if (sweep) {
+            p.strips[atomicAdd(p.nref, 1)] = make_int2(l, st);
+        } else {
+            const int32_t b = atomicAdd(&p.st[l].ndirect, len);  // packed from the lane's slot_base
+            for (int32_t q = 0; q < len; ++q) p.dlist[L.slot_base + b + q] = g + q;
+        }
         for (int32_t q = 0; q < len; ++q) p.route[g + q] = sweep ? 0 : 1;
     }
 }
@@ -178,9 +184,10 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
         const Lane& L = p.lanes[l];
         const int64_t N = L.N;
         const int64_t j0 = int64_t(t) * kRC;
-        if (tid < kRS) {
-            const int64_t g = gbase + tid;
-            if (j0 < N && p.route[g] == 1 && !__ldcg(&p.dead[g])) atomicOr(&alive_s, 1);
+        // entries [gbase, gbase+64) of the lane's packed direct list
+        const int32_t nd = p.st[l].ndirect - int32_t(gbase - L.slot_base);
+        if (tid < kRS && tid < nd && j0 < N) {
+            if (!__ldcg(&p.dead[p.dlist[gbase + tid]])) atomicOr(&alive_s, 1);
         }
         __syncthreads();
         if (!alive_s) {
@@ -204,8 +211,9 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
         for (int k0 = 0; k0 < L.kpad; k0 += kKC) {
             for (int e = tid; e < kRS * kKC / 4; e += 256) {
                 const int s = e / (kKC / 4), q = (e % (kKC / 4)) * 4;
-                *reinterpret_cast<float4*>(&As[s][q]) =
-                    *reinterpret_cast<const float4*>(p.acen + (gbase + s) * int64_t(p.kpad_max) + k0 + q);
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (s < nd) v = *reinterpret_cast<const float4*>(p.acen + int64_t(p.dlist[gbase + s]) * p.kpad_max + k0 + q);
+                *reinterpret_cast<float4*>(&As[s][q]) = v;
             }
             for (int x = tid; x < kRC + kKC + 16; x += 256) {
                 const int64_t idx = j0 + k0 + x;
@@ -248,8 +256,9 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
         }
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
-            const int64_t g = gbase + 8 * w + s;
-            const bool sok = p.route[g] == 1;
+            const int e = 8 * w + s;
+            const bool sok = e < nd;
+            const int64_t g = sok ? p.dlist[gbase + e] : 0;
             const int32_t ci = sok ? p.slot_win[g] : 0;
             const float invc = sok ? win[ci].z : 0.f;
             const float sa = sok ? p.asum[g] : 0.f;

@@ -1,6 +1,6 @@
 // Per-lane results (Sec. 2.2 and Sec. 5):
-//  k_round_reset  clears the window -> slot map and the per-strip survivor
-//                 counts of every lane before a refine round.
+//  k_round_cleanup undoes a refine round's window -> slot map and per-strip
+//                 survivor counts.
 //  k_gather       range discords of the lane: live survivors whose FP64
 //                 nearest-neighbour distance is >= r (Sec. 2.1), appended in
 //                 ascending index order to the lane's discord list.
@@ -18,12 +18,17 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 
-__global__ void k_round_reset(const Pass p) {
-    const Lane& L = p.lanes[blockIdx.y];
-    const int64_t ns = (L.N + kStripH - 1) / kStripH;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < L.N; i += int64_t(gridDim.x) * blockDim.x) {
-        L.slot_of[i] = -1;
-        if (i < ns) L.scount[i] = 0;
+// Undo the round's window -> slot map and per-strip counts (both stay -1 /
+// 0 between rounds, so only the entries a round wrote need clearing).
+__global__ void k_round_cleanup(const Pass p) {
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < p.nslots; g += gridDim.x * blockDim.x) {
+        const int l = p.slot_lane[g];
+        const Lane& L = p.lanes[l];
+        if (g == L.slot_base) p.st[l].ndirect = 0;
+        const int32_t w = p.slot_win[g];
+        if (w < 0) continue;
+        L.slot_of[w] = -1;
+        L.scount[w / kStripH] = 0;
     }
 }
 
@@ -168,10 +173,10 @@ __global__ void k_finalize(const Pass p) {
 
 }  // namespace
 
-cudaError_t launch_round_reset(const Pass& p, cudaStream_t s) {
-    int64_t gx = (p.nmax + 255) / 256;
-    if (gx > 64) gx = 64;
-    k_round_reset<<<dim3(unsigned(gx), unsigned(p.nl)), 256, 0, s>>>(p);
+cudaError_t launch_round_cleanup(const Pass& p, cudaStream_t s) {
+    if (p.nslots <= 0) return cudaSuccess;
+    const int grid = int(min64((int64_t(p.nslots) + 255) / 256, 1024));
+    k_round_cleanup<<<grid, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

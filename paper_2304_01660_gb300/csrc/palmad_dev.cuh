@@ -90,6 +90,8 @@ struct LaneState {
     int32_t got;           // top-K picks
     int32_t count_final;   // range discords at the final r (finalize)
     uint32_t maxerr;       // enc_f32 of the largest |rho_fp32 - rho_fp64| seen
+    int32_t ndirect;       // survivors of this refine round routed to the direct form
+    int32_t pad;
 };
 
 // Everything a pass kernel needs, passed by value.
@@ -111,6 +113,7 @@ struct Pass {
     int32_t* slot_lane;    // [slots] lane of each slot
     int32_t* slot_win;     // [slots] window of each slot, -1 for padding
     int32_t* route;        // [slots] 0 sweep, 1 direct, -1 none
+    int32_t* dlist;        // [slots] direct-form slots of each lane, packed from its slot_base
     float* acen;           // [slots][kpad_max] centred survivor windows
     float* asum;           // [slots]
     uint32_t* gmax;        // [slots] enc_f32 of the maximum rho
@@ -168,7 +171,7 @@ cudaError_t launch_plan(const Pass& p, cudaStream_t s);
 cudaError_t launch_refine_sweep(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_refine_direct(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_recheck(const Pass& p, int grid, cudaStream_t s);
-cudaError_t launch_round_reset(const Pass& p, cudaStream_t s);
+cudaError_t launch_round_cleanup(const Pass& p, cudaStream_t s);
 cudaError_t launch_gather(const Pass& p, cudaStream_t s);
 cudaError_t launch_topk(const Pass& p, cudaStream_t s);
 cudaError_t launch_finalize(const Pass& p, cudaStream_t s);
