@@ -37,6 +37,11 @@ METRIC = "points x lengths / s (all lengths minL..maxL, exact discords)"
 UNIT = "points*lengths/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) per launch of a kernel from an ncu capture of the
+# current kernel source (profiles/); None once the kernel changes.
+TRAFFIC_PER_LAUNCH: dict[str, float | None] = {
+    "refine_sweep": 2.06464e6 + 1.536e3,  # profiles/k_sweep_sine100k.md
+}
 
 
 def _peaks():
@@ -267,17 +272,27 @@ def run_ours(args, w):
 
     if rank == 0:
         peaks = _peaks()
+        # FP32 / FP64 FMA throughput measured on this GPU after the timed region
+        fp_peaks = {}
+        for kind in ("fp32", "fp32x2", "fp64"):
+            try:
+                fp_peaks[kind] = palmad.palmad_measure_peak(local, kind)
+            except Exception:
+                fp_peaks[kind] = None
+        meas = max([v for k2, v in fp_peaks.items() if k2 != "fp64" and v] or [0.0])
+        peak = meas if meas > 0 else FP32_PEAK_TFLOPS
+        peak_src = ("measured: best of scalar and packed (f32x2) FMA chains on this GPU (palmad_measure_peak)"
+                    if meas > 0 else "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (measurement failed)")
         # dominant kernel by event time over the timed region
         dom = max(kernel_ms, key=lambda k2: kernel_ms[k2]) if any(kernel_ms.values()) else "none"
         launches_per = {k2: v for k2, v in last_stats["launches"].items()}
         if dom in flops and kernel_ms.get(dom, 0) > 0:
             ach = flops[dom] / (kernel_ms[dom] / 1e3) / 1e12
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)"}
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": TRAFFIC_PER_LAUNCH.get(dom), "peak_source": peak_src}
         else:
-            roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": None, "traffic": None}
+            roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s",
+                    "frac": None, "traffic": None, "peak_source": peak_src}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -303,6 +318,7 @@ def run_ours(args, w):
                           "passes_per_step": r["stats"]["device_passes"]} for f, r in results.items()},
             "max_fp32_rho_err": last_stats["max_fp32_rho_err"],
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
+            "fma_peaks_tflops": fp_peaks,
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, args.cpu_budget)

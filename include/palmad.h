@@ -242,6 +242,19 @@ palmad_status palmad_topk_profile_noalloc(const double *nn_dev, int64_t N, int32
 /* Counters of the most recent find/drag call on this context. */
 palmad_status palmad_get_stats(const palmad_ctx *ctx, palmad_stats *out);
 
+/*
+ * Measured arithmetic throughput of GPU `device` in TFLOP/s (2 flops per
+ * fused multiply-add lane): the best of five timed launches of independent
+ * FMA chains filling every SM.  It denominates the roofline of the pair
+ * kernels, which are bound by FP32 arithmetic.  Synchronises the device;
+ * allocates and frees a small buffer; not for a hot path.
+ *   kind  PALMAD_PEAK_FP32 (scalar fma.rn.f32), PALMAD_PEAK_FP32X2 (packed
+ *         fma.rn.f32x2) or PALMAD_PEAK_FP64.
+ * Errors: PALMAD_ERR_ARG for a NULL pointer or unknown kind, PALMAD_ERR_CUDA.
+ */
+typedef enum { PALMAD_PEAK_FP32 = 0, PALMAD_PEAK_FP32X2 = 1, PALMAD_PEAK_FP64 = 2 } palmad_peak_kind;
+palmad_status palmad_measure_peak(int device, int32_t kind, double *tflops);
+
 /* Library version string. */
 const char *palmad_version(void);
 

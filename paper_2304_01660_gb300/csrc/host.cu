@@ -93,7 +93,7 @@ struct palmad_ctx {
     // refine pool
     int32_t pool = 0;
     int32_t pool_kpad = 0, pool_nchunks = 0;
-    DBuf<int32_t> slot_lane, slot_win, route, dlist, dead;
+    DBuf<int32_t> slot_lane, slot_win, route, dlist, dgroups, dead;
     bool sets_dirty = false;       // a pass stopped early: slot maps may not be clean
     DBuf<float> acen, asum, cmax;
     DBuf<uint32_t> gmax;
@@ -309,7 +309,7 @@ palmad_status ensure_pool(palmad_ctx* ctx, int32_t kpad, int32_t nchunks) {
     slots = std::min<int64_t>(slots, 1 << 17);
     slots = std::max<int64_t>(64, (slots / 64) * 64);
     CKS(ensure(ctx, ctx->slot_lane, slots)); CKS(ensure(ctx, ctx->slot_win, slots)); CKS(ensure(ctx, ctx->route, slots));
-    CKS(ensure(ctx, ctx->dlist, slots));
+    CKS(ensure(ctx, ctx->dlist, slots)); CKS(ensure(ctx, ctx->dgroups, slots / 64 + 1));
     CKS(ensure(ctx, ctx->dead, slots)); CKS(ensure(ctx, ctx->asum, slots)); CKS(ensure(ctx, ctx->gmax, slots));
     CKS(ensure(ctx, ctx->nn2, slots));
     CKS(ensure(ctx, ctx->acen, size_t(slots) * kpad));
@@ -334,6 +334,7 @@ Pass base_pass(palmad_ctx* ctx, int nl, int K, bool exclusive, const palmad_opti
     p.slot_win = ctx->slot_win.p;
     p.route = ctx->route.p;
     p.dlist = ctx->dlist.p;
+    p.dgroups = ctx->dgroups.p;
     p.acen = ctx->acen.p;
     p.asum = ctx->asum.p;
     p.gmax = ctx->gmax.p;
@@ -945,7 +946,7 @@ void palmad_destroy(palmad_ctx* ctx) {
     for (LaneSet& s : ctx->sets) release_set(s);
     release(ctx->lanes); release(ctx->st); release(ctx->chain); release(ctx->small);
     release(ctx->pidx); release(ctx->pnn);
-    release(ctx->slot_lane); release(ctx->slot_win); release(ctx->route); release(ctx->dlist); release(ctx->dead);
+    release(ctx->slot_lane); release(ctx->slot_win); release(ctx->route); release(ctx->dlist); release(ctx->dgroups); release(ctx->dead);
     release(ctx->acen); release(ctx->asum); release(ctx->cmax); release(ctx->gmax); release(ctx->nn2);
     release(ctx->strips); release(ctx->init_flags);
     if (ctx->h_lanes) cudaFreeHost(ctx->h_lanes);

@@ -130,6 +130,19 @@ __global__ void k_plan_split(const Pass p) {
     }
 }
 
+// Groups of 64 packed direct slots, listed so the direct refine visits only
+// groups that hold work (count in work[4]).
+__global__ void k_plan_groups(const Pass p) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= p.nl) return;
+    const int32_t nd = p.st[l].ndirect;
+    if (nd <= 0) return;
+    const int32_t ng = (nd + 63) / 64;
+    const int32_t at = atomicAdd(p.work + 4, ng);
+    const int32_t base = p.lanes[l].slot_base;
+    for (int32_t k = 0; k < ng; ++k) p.dgroups[at + k] = base + 64 * k;
+}
+
 // --------------------------------------------------------------- prep
 
 __global__ void k_prep(const Pass p) {
@@ -165,7 +178,7 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
     __shared__ int64_t item_s;
     __shared__ int alive_s;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int64_t ngroups = p.nslots / kRS;
+    const int64_t ngroups = *reinterpret_cast<volatile int32_t*>(p.work + 4);
     const int64_t ntiles = (p.nmax + kRC - 1) / kRC;
     const int64_t nitems = ngroups * ntiles;
     unsigned long long pairs = 0;
@@ -178,7 +191,7 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
         __syncthreads();
         const int64_t item = item_s;
         if (item >= nitems) break;
-        const int64_t gbase = (item / ntiles) * kRS;
+        const int64_t gbase = p.dgroups[item / ntiles];
         const int32_t t = int32_t(item % ntiles);
         const int l = p.slot_lane[gbase];
         const Lane& L = p.lanes[l];
@@ -411,6 +424,7 @@ cudaError_t launch_plan(const Pass& p, cudaStream_t s) {
     const int grid = int(min64((int64_t(p.nslots) + block - 1) / block, 1024));
     k_plan_count<<<grid, block, 0, s>>>(p);
     k_plan_split<<<grid, block, 0, s>>>(p);
+    k_plan_groups<<<(p.nl + block - 1) / block, block, 0, s>>>(p);
     const int pgrid = int(min64((int64_t(p.nslots) * 32 + block - 1) / block, 4096));
     k_prep<<<pgrid, block, 0, s>>>(p);
     return cudaGetLastError();

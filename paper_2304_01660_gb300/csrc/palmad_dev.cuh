@@ -114,6 +114,7 @@ struct Pass {
     int32_t* slot_win;     // [slots] window of each slot, -1 for padding
     int32_t* route;        // [slots] 0 sweep, 1 direct, -1 none
     int32_t* dlist;        // [slots] direct-form slots of each lane, packed from its slot_base
+    int32_t* dgroups;      // [slots/64] first dlist entry of every 64-entry group holding direct slots
     float* acen;           // [slots][kpad_max] centred survivor windows
     float* asum;           // [slots]
     uint32_t* gmax;        // [slots] enc_f32 of the maximum rho

@@ -103,9 +103,10 @@ def load(path: str = LIB_PATH):
                                 ctypes.POINTER(Options), _vp, _vp, ctypes.c_int64, _i64p]
     lib.palmad_topk_profile_noalloc.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                 ctypes.c_int32, _vp, _vp, _vp, _vp]
+    lib.palmad_measure_peak.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
     for name in ("palmad_default_options", "palmad_create", "palmad_get_stats", "palmad_find_discords",
                  "palmad_find_discords_device", "palmad_find_discords_batch", "palmad_drag",
-                 "palmad_topk_profile_noalloc"):
+                 "palmad_topk_profile_noalloc", "palmad_measure_peak"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -142,6 +143,19 @@ def palmad_topk_profile_noalloc(nn_dev, m: int, r: float, K: int, exclusive: boo
     if st != PALMAD_OK:
         raise PalmadError(st, "palmad_topk_profile_noalloc failed")
     return idx, nn, cnt
+
+
+PEAK_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
+
+
+def palmad_measure_peak(device: int = 0, kind: str = "fp32") -> float:
+    """Measured FMA throughput of `device` in TFLOP/s (kind: fp32, fp32x2
+    or fp64)."""
+    v = ctypes.c_double(0.0)
+    st = load().palmad_measure_peak(device, PEAK_KINDS[kind], ctypes.byref(v))
+    if st != PALMAD_OK:
+        raise PalmadError(st, "palmad_measure_peak failed")
+    return v.value
 
 
 def _ptr(a) -> int:
