@@ -168,7 +168,7 @@ palmad_status clear_maps(palmad_ctx* ctx, LaneSet& s) {
 
 palmad_status ensure_set(palmad_ctx* ctx, LaneSet& s, int64_t N) {
     if (s.cap >= N) return PALMAD_OK;
-    const int64_t P = (N + 31) / 32, S = (N + kStripH - 1) / kStripH + 1;
+    const int64_t P = (N + 31) / 32, S = (N + kRefineH - 1) / kRefineH + 1;
     CKS(ensure(ctx, s.mu, N)); CKS(ensure(ctx, s.var, N)); CKS(ensure(ctx, s.win, N));
     CKS(ensure(ctx, s.bits0, P)); CKS(ensure(ctx, s.bits, P));
     CKS(ensure(ctx, s.surv, N)); CKS(ensure(ctx, s.slot_of, N)); CKS(ensure(ctx, s.scount, S));

@@ -101,7 +101,7 @@ __global__ void k_plan_count(const Pass p) {
         const int32_t w = L.surv[k];
         p.slot_win[g] = w;
         L.slot_of[w] = g;
-        const int32_t st = w / kStripH;
+        const int32_t st = w / kRefineH;
         atomicAdd(&L.scount[st], 1);                              // survivors of the strip
         if (L.win[w].z == 0.f) atomicOr(&L.scount[st], 1 << 30);  // a flat window among them
     }
@@ -114,11 +114,11 @@ __global__ void k_plan_split(const Pass p) {
         const int l = p.slot_lane[g];
         const Lane& L = p.lanes[l];
         const int32_t k = L.k_lo + (g - L.slot_base);
-        const int32_t st = w / kStripH;
-        if (k > L.k_lo && L.surv[k - 1] / kStripH == st) continue;  // not the first of its strip
+        const int32_t st = w / kRefineH;
+        if (k > L.k_lo && L.surv[k - 1] / kRefineH == st) continue;  // not the first of its strip
         const int32_t c = L.scount[st];
         const int32_t len = c & ((1 << 30) - 1);
-        const int32_t thr = max(2, (5 * kStripH + 2 * L.m - 1) / L.m);  // sweep when cheaper than direct
+        const int32_t thr = max(2, (5 * kRefineH + 2 * L.m - 1) / L.m);  // sweep when cheaper than direct
         const int sweep = (len >= thr && !(c >> 30)) ? 1 : 0;
         if (sweep) {
             p.strips[atomicAdd(p.nref, 1)] = make_int2(l, st);

@@ -1,7 +1,8 @@
 // Strip sweeps: candidate select (DRAG phase 1; Algorithm 3, Sec. 3.2) and
 // the recurrence form of refine (DRAG phase 2; Algorithm 4, Sec. 3.3).
 //
-// A warp owns a strip of H = 32*D consecutive windows (rows i) and steps
+// A warp owns a strip of H = 32*D consecutive windows (rows i; D = 8 in
+// select, 4 in refine) and steps
 // across a range of windows (columns j), 32 columns per chunk:
 //   * lane l holds rows i0 + l*D .. i0 + l*D + D-1 in registers; one step
 //     advances every row by one column with the diagonal recurrence of Eq. 9
@@ -171,7 +172,7 @@ __device__ __forceinline__ void first_col_seeds(const LaneView& a, int64_t r0, i
 }
 
 template <int D, bool REFINE>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const Pass p) {
+__global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(const Pass p) {
     constexpr int H = 32 * D;
     extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -305,37 +306,41 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_sweep(const Pass p) {
             if (REFINE) masked = !(c0 >= i0 + H - 1 + m || c0 + 31 <= i0 - m);
             else masked = (c0 - ja) < int64_t(H - 1);
             uint32_t colmask = 0;
-            for (int st = st0; st < steps; ++st) {
+            // One column step: every row advances along its diagonal (Eq. 9),
+            // then rho (up to the row factor) feeds the row maxima and, in
+            // select, the column mark.
+            auto step = [&](int st, bool first_col, bool mask) {
                 const int64_t j = c0 + st;
                 const float4 cr = crb[st];
                 const float sd = sm.seed[st];
                 const float up = __shfl_up_sync(kFull, cov[D - 1], 1);
-                if (!REFINE || j != ja) {
+                if (!first_col) {
 #pragma unroll
                     for (int d = D - 1; d >= 1; --d) cov[d] = fmaf(df_r[d], cr.y, fmaf(cr.x, dg_r[d], cov[d - 1]));
                     cov[0] = (lane == 0) ? sd : fmaf(df_r[0], cr.y, fmaf(cr.x, dg_r[0], up));
                 }
                 bool pred = false;
-                if (masked) {
-                    const int64_t lim = j - r0;  // j - i for d = 0
+                const int64_t lim = j - r0;  // j - i for d = 0
 #pragma unroll
-                    for (int d = 0; d < D; ++d) {
-                        float x = cov[d] * cr.z;
+                for (int d = 0; d < D; ++d) {
+                    float x = cov[d] * cr.z;
+                    if (mask) {
                         const int64_t dj = lim - d;  // j - i
                         const bool ok = REFINE ? (dj >= m || dj <= -int64_t(m)) : (dj >= m);
                         x = ok ? x : -kInf;
-                        rmax[d] = fmaxf(rmax[d], x);
-                        if (!REFINE) pred |= x > thr_r[d];
                     }
-                } else {
-#pragma unroll
-                    for (int d = 0; d < D; ++d) {
-                        const float x = cov[d] * cr.z;
-                        rmax[d] = fmaxf(rmax[d], x);
-                        if (!REFINE) pred |= x > thr_r[d];
-                    }
+                    rmax[d] = fmaxf(rmax[d], x);
+                    if (!REFINE) pred |= x > thr_r[d];
                 }
                 if (!REFINE && pred) colmask |= 1u << st;
+            };
+            if (!masked && st0 == 0 && steps == 32 && !(REFINE && c0 == ja)) {
+                // full unmasked chunk: unrolled so loads and FMAs of
+                // consecutive steps interleave
+#pragma unroll
+                for (int st = 0; st < 32; ++st) step(st, false, false);
+            } else {
+                for (int st = st0; st < steps; ++st) step(st, REFINE && c0 + st == ja, masked);
             }
             if (lane == 0) {
                 seeds += 32;
@@ -400,8 +405,8 @@ size_t sweep_smem(const Pass& p) {
 
 template <bool REFINE>
 cudaError_t launch_sweep_impl(const Pass& p, int grid, cudaStream_t s) {
-    constexpr int D = 8;
-    static_assert(32 * D == kStripH, "strip height");
+    constexpr int D = (REFINE ? kRefineH : kStripH) / 32;
+    static_assert(32 * D == (REFINE ? kRefineH : kStripH), "strip height");
     const size_t sm = sweep_smem(p);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_sweep<D, REFINE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));

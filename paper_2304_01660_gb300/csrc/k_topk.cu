@@ -28,7 +28,7 @@ __global__ void k_round_cleanup(const Pass p) {
         const int32_t w = p.slot_win[g];
         if (w < 0) continue;
         L.slot_of[w] = -1;
-        L.scount[w / kStripH] = 0;
+        L.scount[w / kRefineH] = 0;
     }
 }
 

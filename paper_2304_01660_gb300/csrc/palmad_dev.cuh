@@ -20,7 +20,8 @@ namespace palmad {
 
 constexpr int kWarp = 32;
 constexpr float kInf = __builtin_huge_valf();
-constexpr int kStripH = 256;   // rows per strip of the sweeps (32 lanes x 8)
+constexpr int kStripH = 256;   // rows per strip of the select sweep (32 lanes x 8)
+constexpr int kRefineH = 128;  // rows per strip of the refine sweep (32 lanes x 4)
 constexpr int kMaxK = 1024;    // largest top-K
 
 // Per-window data the FP32 kernels read, one 16-byte record per window:
@@ -63,7 +64,7 @@ struct Lane {
     uint32_t* bits;        // working candidate bitmap
     int32_t* surv;         // survivors of select, ascending
     int32_t* slot_of;      // window -> pool slot of this round, -1 otherwise
-    int32_t* scount;       // per strip: survivors this round (+ flat flag in bit 30)
+    int32_t* scount;       // per refine strip: survivors this round (+ flat flag in bit 30)
     int32_t* didx;         // range discords found (ascending), with
     double* dnn;           //   their FP64 nearest-neighbour distances
     float* heat;           // heatmap row or nullptr
