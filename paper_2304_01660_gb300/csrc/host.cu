@@ -383,6 +383,7 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     ctx->sets_dirty = true;
     Pass p = base_pass(ctx, nl, K, exclusive, o);
     p.sel_items = strips;
+    p.sel_pieces = int32_t((kStripH + 31 + p.cap + kSelPieceCols - 1) / kSelPieceCols);
     p.nmax = nmax;
     p.kpad_max = ctx->pool_kpad;
     p.nchunks_max = ctx->pool_nchunks;

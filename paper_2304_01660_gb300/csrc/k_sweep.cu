@@ -190,7 +190,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
     // refine items: rank k (0, +1, -1, +2, -2, ... segments away from the
     // strip's own segment) major, strip minor -- the segments nearest every
     // strip run first, so survivors pruned there skip the far ones
-    const int64_t nitems = REFINE ? nref * 2 * nseg : p.sel_items;
+    // select items: column piece major, strip minor -- every strip's first
+    // piece (its triangle and what follows) runs before any second piece, so
+    // a later piece usually finds its rows already dead and is skipped, and
+    // no single strip's scan holds the launch open
+    const int64_t nitems = REFINE ? nref * 2 * nseg : p.sel_items * int64_t(p.sel_pieces);
     unsigned long long pairs = 0, seeds = 0;
 
     for (;;) {
@@ -200,15 +204,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
         if (item >= nitems) break;
         int l;
         int64_t s;
-        int64_t kq = 0;
+        int64_t kq = 0, piece = 0;
         if (REFINE) {
             const int2 e = p.strips[item % nref];
             l = e.x;
             s = e.y;
             kq = item / nref;
         } else {
-            l = lane_of(strip_base, p.nl, item);
-            s = item - strip_base[l];
+            piece = item / p.sel_items;
+            const int64_t si = item % p.sel_items;
+            l = lane_of(strip_base, p.nl, si);
+            s = si - strip_base[l];
         }
         const Lane& Lg = p.lanes[l];
         const LaneView a{Lg.T, Lg.n, Lg.N, Lg.m, Lg.win};
@@ -216,7 +222,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
         const int64_t N = a.N;
         const int kp = ((m + 127) / 128) * 128;
         const float rho_prune = rho_prune_of(Lg, p.st[l]);
-        int64_t ja, jb;
+        // [ja, jb): columns of this item; jt: first column right of the
+        // exclusion zone of the top row (select's triangle starts there)
+        int64_t ja, jb, jt = 0;
         if (REFINE) {
             const int64_t q0 = (s * H + H / 2) / p.seg;
             const int64_t d = (kq + 1) / 2;
@@ -225,10 +233,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
             if (q < 0 || ja >= N) continue;
             jb = min64(N, ja + p.seg);
         } else {
-            ja = s * H + m;
-            if (ja >= N) continue;  // no window to the right: column marks / refine decide these rows
-            jb = min64(N, s * H + H - 1 + m + p.cap);
+            jt = s * H + m;
+            if (jt >= N) continue;  // no window to the right: column marks / refine decide these rows
+            const int64_t pc = (jt & ~int64_t(31)) + piece * int64_t(kSelPieceCols);
+            ja = piece == 0 ? jt : pc;
+            jb = min64(min64(N, s * H + H - 1 + m + p.cap), pc + kSelPieceCols);
+            if (ja >= jb) continue;
         }
+        // rows start from directly computed dot products at column ja
+        // (refine, and select pieces after the first)
+        const bool seeded = REFINE || piece > 0;
         uint32_t* bits = Lg.bits;
         const int32_t* slot_of = Lg.slot_of;
         const int64_t i0 = s * H;
@@ -277,10 +291,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
         __syncwarp();
 
         float tmax[D];
-        if (REFINE) {
-            first_col_seeds<D>(a, r0, ja, cov);
 #pragma unroll
-            for (int d = 0; d < D; ++d) tmax[d] = -kInf;
+        for (int d = 0; d < D; ++d) tmax[d] = -kInf;
+        if (seeded) {
+            first_col_seeds<D>(a, r0, ja, cov);
             seeds += H;
         }
         const int64_t rows = min64(H, N - i0);
@@ -304,7 +318,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
             const int st0 = int(max64(0, ja - c0));
             bool masked;
             if (REFINE) masked = !(c0 >= i0 + H - 1 + m || c0 + 31 <= i0 - m);
-            else masked = (c0 - ja) < int64_t(H - 1);
+            else masked = (c0 - jt) < int64_t(H - 1);
             uint32_t colmask = 0;
             // One column step: every row advances along its diagonal (Eq. 9),
             // then rho (up to the row factor) feeds the row maxima and, in
@@ -334,20 +348,20 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
                 }
                 if (!REFINE && pred) colmask |= 1u << st;
             };
-            if (!masked && st0 == 0 && steps == 32 && !(REFINE && c0 == ja)) {
+            if (!masked && st0 == 0 && steps == 32 && !(seeded && c0 == ja)) {
                 // full unmasked chunk: unrolled so loads and FMAs of
                 // consecutive steps interleave
 #pragma unroll
                 for (int st = 0; st < 32; ++st) step(st, false, false);
             } else {
-                for (int st = st0; st < steps; ++st) step(st, REFINE && c0 + st == ja, masked);
+                for (int st = st0; st < steps; ++st) step(st, seeded && c0 + st == ja, masked);
             }
             if (lane == 0) {
                 seeds += 32;
                 if (REFINE) pairs += uint64_t(rows) * uint64_t(steps - st0);
                 else
                     for (int st = st0; st < steps; ++st) {
-                        const int64_t v = min64(rows, c0 + st - ja + 1);
+                        const int64_t v = min64(rows, c0 + st - jt + 1);
                         if (v > 0) pairs += uint64_t(v);
                     }
             }

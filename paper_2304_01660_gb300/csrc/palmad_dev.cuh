@@ -22,6 +22,7 @@ constexpr int kWarp = 32;
 constexpr float kInf = __builtin_huge_valf();
 constexpr int kStripH = 256;   // rows per strip of the select sweep (32 lanes x 8)
 constexpr int kRefineH = 128;  // rows per strip of the refine sweep (32 lanes x 4)
+constexpr int kSelPieceCols = 512;  // columns per select work item (a strip's scan is cut into pieces)
 constexpr int kMaxK = 1024;    // largest top-K
 
 // Per-window data the FP32 kernels read, one 16-byte record per window:
@@ -105,6 +106,8 @@ struct Pass {
     int32_t seg;           // refine sweep columns per work item (multiple of 256)
     int64_t cap;           // select columns per strip past its triangle
     int64_t sel_items;     // total select strips
+    int32_t sel_pieces;    // column pieces per select strip
+    int32_t pad3;
     int64_t nmax;          // largest N over the lanes
     // refine pool (this round)
     int32_t nslots;        // slots in use this round (64-aligned per lane)
