@@ -190,7 +190,8 @@ def run_ours(args, w):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     prof = 0 if args.no_events else 1
     forms = {"plain": palmad.palmad_default_options(profile=prof),
-             "batched": palmad.palmad_default_options(profile=prof, batch_lengths=args.batch)}
+             "batched": palmad.palmad_default_options(profile=prof, batch_lengths=args.batch),
+             "mixed": palmad.palmad_default_options(profile=prof, batch_lengths=args.batch, precision=1)}
     forms = {f: o for f, o in forms.items() if f in args.forms.split(",")}
     best = args.form if args.form in forms else next(iter(forms))
 
@@ -296,9 +297,11 @@ def run_ours(args, w):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32" if best == "mixed" else "f32",
+            "data": "synthetic",
             "config": {"workload": w.name, "n": n, "minL": minL, "maxL": maxL, "topK": K,
-                       "form": f"batched W={args.batch}" if best == "batched" else "plain",
+                       "form": {"plain": "plain FP32", "batched": f"batched W={args.batch} FP32",
+                                "mixed": f"mixed precision (tensor-core direct refine) + batched W={args.batch}"}[best],
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
@@ -340,9 +343,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end leg")
     ap.add_argument("--no-events", action="store_true", help="no per-launch CUDA events (profiler runs)")
-    ap.add_argument("--form", choices=["plain", "batched"], default="batched", help="form reported as `value`")
+    ap.add_argument("--form", choices=["plain", "batched", "mixed"], default="mixed", help="form reported as `value`")
     ap.add_argument("--batch", type=int, default=16, help="lengths per pass of the batched form")
-    ap.add_argument("--forms", default="plain,batched", help="forms to time (comma separated)")
+    ap.add_argument("--forms", default="plain,batched,mixed", help="forms to time (comma separated)")
     args = ap.parse_args(argv)
     w = synth.workload(args.workload)
     if args.impl == "reference":

@@ -95,7 +95,10 @@ typedef struct {
     int32_t pool_slots;      /* cap on the survivors refined at once (0 = as many as
                                 about 1 GiB of per-survivor buffers holds); more
                                 survivors are refined in several rounds */
-    int32_t reserved[4];
+    int32_t direct_below;    /* 0: the plan's own split between the refine forms; k > 0:
+                                every strip with fewer than k survivors uses the direct
+                                form (k = 129 sends every survivor there) */
+    int32_t reserved[3];
 } palmad_options;
 
 /* Per-call counters of the most recent find/drag call. */

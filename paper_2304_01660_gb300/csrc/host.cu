@@ -45,7 +45,8 @@ struct DBuf {
 struct Small {
     int32_t work[8];
     int32_t nref;
-    int32_t pad[7];
+    int32_t err;         // a bounded device wait gave up
+    int32_t pad[6];
     unsigned long long pairs[8];
 };
 
@@ -244,6 +245,7 @@ palmad_status read_options(palmad_ctx* ctx, const palmad_options* in, palmad_opt
     if (o.select_cap < 0) return fail(ctx, PALMAD_ERR_ARG, "select_cap must be >= 0");
     if (o.batch_lengths < 0 || o.batch_lengths > 1024) return fail(ctx, PALMAD_ERR_ARG, "batch_lengths must lie in [0, 1024]");
     if (o.pool_slots < 0) return fail(ctx, PALMAD_ERR_ARG, "pool_slots must be >= 0");
+    if (o.direct_below < 0) return fail(ctx, PALMAD_ERR_ARG, "direct_below must be >= 0");
     return PALMAD_OK;
 }
 
@@ -344,6 +346,7 @@ Pass base_pass(palmad_ctx* ctx, int nl, int K, bool exclusive, const palmad_opti
     p.strips = ctx->strips.p;
     p.nref = &ctx->small.p->nref;
     p.work = ctx->small.p->work;
+    p.err = &ctx->small.p->err;
     p.pairs = ctx->small.p->pairs;
     p.pick_idx = ctx->pidx.p;
     p.pick_nn = ctx->pnn.p;
@@ -387,6 +390,8 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     p.nmax = nmax;
     p.kpad_max = ctx->pool_kpad;
     p.nchunks_max = ctx->pool_nchunks;
+    p.mixed = (o.precision == PALMAD_PREC_MIXED && refine_tc_supported(p)) ? 1 : 0;
+    p.direct_below = o.direct_below;
 
     CK(cudaMemcpyAsync(ctx->lanes.p, ctx->h_lanes, sizeof(Lane) * nl, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->st.p, ctx->h_st, sizeof(LaneState) * nl, cudaMemcpyHostToDevice, ctx->stream));
@@ -430,7 +435,8 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
         CK(cudaMemsetAsync(&ctx->small.p->nref, 0, sizeof(int32_t), ctx->stream));
         LAUNCH(PALMAD_K_PLAN, launch_plan(p, ctx->stream));
         LAUNCH(PALMAD_K_REFINE_SWEEP, launch_refine_sweep(p, ctx->sms * 4, ctx->stream));
-        LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_direct(p, ctx->sms * 2, ctx->stream));
+        if (p.mixed) LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_tc(p, ctx->sms, ctx->stream));
+        else LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_direct(p, ctx->sms * 2, ctx->stream));
         LAUNCH(PALMAD_K_RECHECK, launch_recheck(p, ctx->sms * 8, ctx->stream));
         LAUNCH(PALMAD_K_GATHER, launch_gather(p, ctx->stream));
         LAUNCH(PALMAD_K_PLAN, launch_round_cleanup(p, ctx->stream));
@@ -449,6 +455,7 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     out.idx.assign(ctx->h_pidx, ctx->h_pidx + int64_t(nl) * K);
     out.nn.assign(ctx->h_pnn, ctx->h_pnn + int64_t(nl) * K);
     const Small& sm = *ctx->h_small;
+    if (sm.err) return fail(ctx, PALMAD_ERR_TIMEOUT, "tensor-core refine: an MMA did not signal completion");
     ctx->stats.select_pairs += int64_t(sm.pairs[0]);
     ctx->stats.refine_pairs += int64_t(sm.pairs[1]) + int64_t(sm.pairs[4]);
     ctx->stats.fp64_pairs += int64_t(sm.pairs[2]);

@@ -118,7 +118,14 @@ __global__ void k_plan_split(const Pass p) {
         if (k > L.k_lo && L.surv[k - 1] / kRefineH == st) continue;  // not the first of its strip
         const int32_t c = L.scount[st];
         const int32_t len = c & ((1 << 30) - 1);
-        const int32_t thr = max(2, (5 * kRefineH + 2 * L.m - 1) / L.m);  // sweep when cheaper than direct
+        // sweep when cheaper than the direct form: FP32 direct costs 2m flops per
+        // survivor-column against ~5 per row-column of the sweep.  The
+        // tensor-core direct form takes only lone survivors: measured on the
+        // sine, random-walk and multi-series workloads, any larger share ran
+        // slower than the sweep, whose strips stop at the first 32-column
+        // chunk where every row is pruned
+        const int32_t thr = p.direct_below > 0 ? p.direct_below
+                           : (p.mixed ? 2 : max(2, (5 * kRefineH + 2 * L.m - 1) / L.m));
         const int sweep = (len >= thr && !(c >> 30)) ? 1 : 0;
         if (sweep) {
             p.strips[atomicAdd(p.nref, 1)] = make_int2(l, st);

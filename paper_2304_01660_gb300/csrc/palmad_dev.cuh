@@ -107,13 +107,13 @@ struct Pass {
     int64_t cap;           // select columns per strip past its triangle
     int64_t sel_items;     // total select strips
     int32_t sel_pieces;    // column pieces per select strip
-    int32_t pad3;
+    int32_t direct_below;  // > 0: strips with fewer survivors take the direct form
     int64_t nmax;          // largest N over the lanes
     // refine pool (this round)
     int32_t nslots;        // slots in use this round (64-aligned per lane)
     int32_t kpad_max;
     int32_t nchunks_max;   // 32-column chunks of the largest lane
-    int32_t pad;
+    int32_t mixed;         // 1: direct refine on the tensor cores (k_refine_tc)
     int32_t* slot_lane;    // [slots] lane of each slot
     int32_t* slot_win;     // [slots] window of each slot, -1 for padding
     int32_t* route;        // [slots] 0 sweep, 1 direct, -1 none
@@ -127,6 +127,7 @@ struct Pass {
     float* cmax;           // [slots][nchunks_max] maximum rho per 32-column chunk
     int2* strips;          // (lane, strip) swept by refine
     int32_t* nref;
+    int32_t* err;          // set to 1 by a kernel whose bounded wait gave up
     int32_t* work;         // [8] work counters, zeroed per launch group
     unsigned long long* pairs;  // [8] 0 select, 1 direct refine, 2 fp64, 3 select seeds,
                                 //     4 sweep refine, 5 sweep seeds
@@ -175,6 +176,8 @@ cudaError_t launch_compact(const Pass& p, cudaStream_t s);
 cudaError_t launch_plan(const Pass& p, cudaStream_t s);
 cudaError_t launch_refine_sweep(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_refine_direct(const Pass& p, int grid, cudaStream_t s);
+bool refine_tc_supported(const Pass& p);
+cudaError_t launch_refine_tc(const Pass& p, int sms, cudaStream_t s);
 cudaError_t launch_recheck(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_round_cleanup(const Pass& p, cudaStream_t s);
 cudaError_t launch_gather(const Pass& p, cudaStream_t s);

@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
         ("use_graph", ctypes.c_int32),
         ("profile", ctypes.c_int32),
         ("pool_slots", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("direct_below", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 

@@ -1,0 +1,99 @@
+"""GPU parity of the mixed-precision form (tensor-core direct refine) against
+the FP64 oracle, and against the FP32 form.
+
+The mixed form must return exactly what the FP32 form returns: the tensor
+cores only change which FP32-side values bound the pruning and the FP64
+re-check; every kept decision and every reported distance is FP64.  Most
+cases set direct_below = 129, which routes every survivor to the direct
+form, so the tcgen05 kernel sees every lane shape; the m >= 520 cases use
+its 32-survivor variant (kpad > 512).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_01660_gb300 import synth
+
+from test_gpu_parity import NN_RTOL, SERIES, _check_drag, _check_merlin, _opts, _thresholds, ctx  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+MIXED = 1
+ALL_TC = dict(precision=MIXED, direct_below=129)
+
+
+@pytest.mark.parametrize("name", list(SERIES))
+@pytest.mark.parametrize("m", [8, 37, 100])
+def test_mixed_drag_matches_oracle(ctx, name, m):
+    T = SERIES[name]()
+    mp, _ = oracle.matrix_profile(T, m)
+    for r in _thresholds(mp, (0.5, 0.9, 0.99, 1.0)):
+        _check_drag(ctx, T, m, float(r), _opts(**ALL_TC))
+
+
+@pytest.mark.parametrize("m", [520, 600])
+def test_mixed_drag_long_windows(ctx, m):
+    """kpad > 512: 32 survivors per MMA."""
+    T = synth.random_walk(3000, 61)
+    mp, _ = oracle.matrix_profile(T, m)
+    for r in _thresholds(mp, (0.2, 0.9, 1.0)):
+        _check_drag(ctx, T, m, float(r), _opts(**ALL_TC))
+    _check_drag(ctx, T, m, 0.0, _opts(**ALL_TC))
+
+
+def test_mixed_drag_degenerate_thresholds(ctx):
+    T = SERIES["rw3000"]()
+    m = 20
+    N = len(T) - m + 1
+    assert _check_drag(ctx, T, m, 0.0, _opts(**ALL_TC)) == N
+    assert _check_drag(ctx, T, m, 2 * np.sqrt(m) + 1.0, _opts(precision=MIXED)) == 0
+
+
+@pytest.mark.parametrize("route", [0, 129])
+@pytest.mark.parametrize("W", [0, 16])
+@pytest.mark.parametrize("name,minL,maxL,K,excl", [
+    ("rw3000", 10, 40, 2, True),
+    ("sine4000", 50, 70, 3, True),
+    ("flat2200", 16, 30, 1, False),
+])
+def test_mixed_merlin_matches_oracle(ctx, route, W, name, minL, maxL, K, excl):
+    T = SERIES[name]()
+    got = ctx.palmad_find_discords(T, minL, maxL, K, _opts(precision=MIXED, exclusive_topk=int(excl), batch_lengths=W,
+                                                           direct_below=route), heatmap=True)
+    want = oracle.merlin(T, minL, maxL, K, excl, heatmap=True)
+    _check_merlin(got, want, heat=True)
+
+
+def test_mixed_refine_rounds_and_mixed_lengths(ctx):
+    """Many refine rounds (tiny pool) and lanes of different kpad in one pass."""
+    series = [SERIES["rw3000"](), SERIES["sine4000"](), synth.random_walk(2600, 50)]
+    mins, maxs = [10, 40, 100], [30, 60, 140]
+    outs = ctx.palmad_find_discords_batch(series, mins, maxs, 2, _opts(batch_lengths=8, pool_slots=64, **ALL_TC))
+    for T, a, b, o in zip(series, mins, maxs, outs):
+        _check_merlin(o, oracle.merlin(T, a, b, 2, True))
+
+
+def test_mixed_equals_fp32_full_size(ctx):
+    """sine100k, all 129 lengths, batched: identical results in the FP32
+    form, the mixed form, and the mixed form with every survivor on the
+    tensor cores."""
+    w = synth.workload("sine100k")
+    T = w.series[0]
+    args = (T, w.minL[0], w.maxL[0], w.topK)
+    a = ctx.palmad_find_discords(*args, _opts(batch_lengths=16), heatmap=True)
+    for o in (_opts(batch_lengths=16, precision=MIXED), _opts(batch_lengths=16, **ALL_TC)):
+        b = ctx.palmad_find_discords(*args, o, heatmap=True)
+        for k in ("idx", "nn", "count", "r", "heatmap"):
+            np.testing.assert_array_equal(a[k], b[k])
+    st = ctx.palmad_get_stats()
+    assert st["refine_pairs"] > 0
+
+
+@pytest.mark.parametrize("name", ["rw3000", "sine4000", "flat2200"])
+def test_fp32_direct_form_matches_oracle(ctx, name):
+    """Every survivor on the FP32 direct form (direct_below = 129)."""
+    T = SERIES[name]()
+    for m in (8, 37, 100):
+        mp, _ = oracle.matrix_profile(T, m)
+        for r in _thresholds(mp, (0.5, 0.99)):
+            _check_drag(ctx, T, m, float(r), _opts(direct_below=129))
