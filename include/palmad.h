@@ -98,7 +98,12 @@ typedef struct {
     int32_t direct_below;    /* 0: the plan's own split between the refine forms; k > 0:
                                 every strip with fewer than k survivors uses the direct
                                 form (k = 129 sends every survivor there) */
-    int32_t reserved[3];
+    int32_t tc_seed_min;     /* mixed precision: k > 0 gives refine strips with at least k
+                                survivors top-row seeds from the tensor cores; 0 (default)
+                                keeps every seed on the CUDA cores, which measured faster */
+    int32_t seed_rows_max;   /* cap on tensor-core seed rows per refine round (0 = as many
+                                as 1 GiB holds); strips past the cap seed on the CUDA cores */
+    int32_t reserved[1];
 } palmad_options;
 
 /* Per-call counters of the most recent find/drag call. */
@@ -123,6 +128,8 @@ typedef struct {
        (profile == 1 only); index = PALMAD_K_* */
     int64_t launches[12];
     double kernel_ms[12];
+    int64_t seed_pairs;         /* tensor-core top-row seeds computed (strip x column) */
+    double seed_flops;          /* their algorithmic work: 2m per seed */
 } palmad_stats;
 
 /* Kernel ids for palmad_stats.launches / kernel_ms. */
@@ -138,6 +145,7 @@ enum {
     PALMAD_K_TOPK = 8,          /* per-length top-K */
     PALMAD_K_HEAT = 9,          /* heatmap row write (Eq. 10) */
     PALMAD_K_OTHER = 10,
+    PALMAD_K_SEED_TC = 11,      /* tensor-core top-row seeds of the refine sweep */
     PALMAD_K_COUNT = 12
 };
 

@@ -34,6 +34,7 @@ constexpr int kDefaultCap = 512;     // select columns past the strip triangle
 constexpr int kRefineSeg = 512;      // refine sweep columns per work item (multiple of 256)
 constexpr int kMaxLanes = 4096;      // lanes per pass
 constexpr int64_t kPoolBytes = int64_t(1) << 30;  // per-chunk maxima of the refine pool
+constexpr int64_t kSeedBytes = int64_t(1) << 30;  // tensor-core top-row seeds of the refine sweep
 
 template <class T>
 struct DBuf {
@@ -46,7 +47,8 @@ struct Small {
     int32_t work[8];
     int32_t nref;
     int32_t err;         // a bounded device wait gave up
-    int32_t pad[6];
+    int32_t seed_ngroups;
+    int32_t pad[5];
     unsigned long long pairs[8];
 };
 
@@ -94,7 +96,9 @@ struct palmad_ctx {
     // refine pool
     int32_t pool = 0;
     int32_t pool_kpad = 0, pool_nchunks = 0;
-    DBuf<int32_t> slot_lane, slot_win, route, dlist, dgroups, dead;
+    DBuf<int32_t> slot_lane, slot_win, route, dlist, dgroups, dead, strip_row;
+    DBuf<float> topcen, topsum, seeds;
+    DBuf<int4> seed_groups;
     bool sets_dirty = false;       // a pass stopped early: slot maps may not be clean
     DBuf<float> acen, asum, cmax;
     DBuf<uint32_t> gmax;
@@ -246,6 +250,8 @@ palmad_status read_options(palmad_ctx* ctx, const palmad_options* in, palmad_opt
     if (o.batch_lengths < 0 || o.batch_lengths > 1024) return fail(ctx, PALMAD_ERR_ARG, "batch_lengths must lie in [0, 1024]");
     if (o.pool_slots < 0) return fail(ctx, PALMAD_ERR_ARG, "pool_slots must be >= 0");
     if (o.direct_below < 0) return fail(ctx, PALMAD_ERR_ARG, "direct_below must be >= 0");
+    if (o.tc_seed_min < 0) return fail(ctx, PALMAD_ERR_ARG, "tc_seed_min must be >= 0");
+    if (o.seed_rows_max < 0) return fail(ctx, PALMAD_ERR_ARG, "seed_rows_max must be >= 0");
     return PALMAD_OK;
 }
 
@@ -316,7 +322,7 @@ palmad_status ensure_pool(palmad_ctx* ctx, int32_t kpad, int32_t nchunks) {
     CKS(ensure(ctx, ctx->nn2, slots));
     CKS(ensure(ctx, ctx->acen, size_t(slots) * kpad));
     CKS(ensure(ctx, ctx->cmax, size_t(slots) * nchunks));
-    CKS(ensure(ctx, ctx->strips, size_t(slots)));
+    CKS(ensure(ctx, ctx->strips, size_t(slots))); CKS(ensure(ctx, ctx->strip_row, size_t(slots)));
     ctx->pool = int32_t(slots);
     ctx->pool_kpad = kpad;
     ctx->pool_nchunks = nchunks;
@@ -379,6 +385,7 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
         ctx->h_lanes[l] = L;
         LaneState s = req[l].state;
         s.nsurv = 0; s.dcount = 0; s.got = 0; s.count_final = 0; s.maxerr = 0; s.ndirect = 0;
+        s.seed_rows = 0; s.seed_base = 0; s.seed_eff = 0; s.seed_eps = 0;
         if (L.stats_mode != 0) { s.flags = 0; s.ab[0] = 0; s.ab[1] = 0; }
         ctx->h_st[l] = s;
     }
@@ -389,9 +396,33 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     p.sel_pieces = int32_t((kStripH + 31 + p.cap + kSelPieceCols - 1) / kSelPieceCols);
     p.nmax = nmax;
     p.kpad_max = ctx->pool_kpad;
+    p.kpad_pass = kpad_max;
     p.nchunks_max = ctx->pool_nchunks;
     p.mixed = (o.precision == PALMAD_PREC_MIXED && refine_tc_supported(p)) ? 1 : 0;
     p.direct_below = o.direct_below;
+    p.strip_row = ctx->strip_row.p;
+    p.seed_ngroups = &ctx->small.p->seed_ngroups;
+    p.tc_seeds = 0;
+    if (o.precision == PALMAD_PREC_MIXED && o.tc_seed_min > 0 && seed_tc_supported(p)) {
+        // seed rows of nmax columns (rounded to the kernel's 1024-column blocks)
+        const int64_t stride = (nmax + 1023) / 1024 * 1024;
+        int64_t cap = std::min<int64_t>(kSeedBytes / (stride * int64_t(sizeof(float))), ctx->pool);
+        if (o.seed_rows_max > 0) cap = std::min<int64_t>(cap, o.seed_rows_max);
+        if (cap >= 1) {
+            CKS(ensure(ctx, ctx->seeds, size_t(cap * stride)));
+            CKS(ensure(ctx, ctx->topcen, size_t(cap) * p.kpad_max));
+            CKS(ensure(ctx, ctx->topsum, size_t(cap)));
+            CKS(ensure(ctx, ctx->seed_groups, size_t(cap / 32 + nl + 1)));
+            p.tc_seeds = 1;
+            p.seed_min = o.tc_seed_min;
+            p.seeds = ctx->seeds.p;
+            p.topcen = ctx->topcen.p;
+            p.topsum = ctx->topsum.p;
+            p.seed_groups = ctx->seed_groups.p;
+            p.seed_stride = stride;
+            p.seed_cap = int32_t(cap);
+        }
+    }
 
     CK(cudaMemcpyAsync(ctx->lanes.p, ctx->h_lanes, sizeof(Lane) * nl, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->st.p, ctx->h_st, sizeof(LaneState) * nl, cudaMemcpyHostToDevice, ctx->stream));
@@ -431,9 +462,10 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
         if (!any) break;
         p.nslots = used;
         CK(cudaMemcpyAsync(ctx->lanes.p, ctx->h_lanes, sizeof(Lane) * nl, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemsetAsync(&ctx->small.p->work[1], 0, 4 * sizeof(int32_t), ctx->stream));
+        CK(cudaMemsetAsync(&ctx->small.p->work[1], 0, 7 * sizeof(int32_t), ctx->stream));
         CK(cudaMemsetAsync(&ctx->small.p->nref, 0, sizeof(int32_t), ctx->stream));
         LAUNCH(PALMAD_K_PLAN, launch_plan(p, ctx->stream));
+        if (p.tc_seeds) LAUNCH(PALMAD_K_SEED_TC, launch_seeds(p, ctx->sms, ctx->stream));
         LAUNCH(PALMAD_K_REFINE_SWEEP, launch_refine_sweep(p, ctx->sms * 4, ctx->stream));
         if (p.mixed) LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_tc(p, ctx->sms, ctx->stream));
         else LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_direct(p, ctx->sms * 2, ctx->stream));
@@ -466,6 +498,8 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     ctx->stats.select_flops += 5.0 * double(sm.pairs[0]) + 2.0 * mavg * double(sm.pairs[3]);
     ctx->stats.refine_flops += 2.0 * mavg * double(sm.pairs[1]);
     ctx->stats.sweep_flops += 5.0 * double(sm.pairs[4]) + 2.0 * mavg * double(sm.pairs[5]);
+    ctx->stats.seed_pairs += int64_t(sm.pairs[6]);
+    ctx->stats.seed_flops += 2.0 * mavg * double(sm.pairs[6]);
     for (int l = 0; l < nl; ++l) {
         const uint32_t e = out.st[l].maxerr;
         if (e) {
@@ -957,6 +991,7 @@ void palmad_destroy(palmad_ctx* ctx) {
     release(ctx->slot_lane); release(ctx->slot_win); release(ctx->route); release(ctx->dlist); release(ctx->dgroups); release(ctx->dead);
     release(ctx->acen); release(ctx->asum); release(ctx->cmax); release(ctx->gmax); release(ctx->nn2);
     release(ctx->strips); release(ctx->init_flags);
+    release(ctx->strip_row); release(ctx->topcen); release(ctx->topsum); release(ctx->seeds); release(ctx->seed_groups);
     if (ctx->h_lanes) cudaFreeHost(ctx->h_lanes);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     if (ctx->h_chain) cudaFreeHost(ctx->h_chain);

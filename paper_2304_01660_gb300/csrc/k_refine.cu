@@ -128,7 +128,9 @@ __global__ void k_plan_split(const Pass p) {
                            : (p.mixed ? 2 : max(2, (5 * kRefineH + 2 * L.m - 1) / L.m));
         const int sweep = (len >= thr && !(c >> 30)) ? 1 : 0;
         if (sweep) {
-            p.strips[atomicAdd(p.nref, 1)] = make_int2(l, st);
+            const int32_t e = atomicAdd(p.nref, 1);
+            p.strips[e] = make_int2(l, st);
+            if (p.tc_seeds) p.strip_row[e] = len >= p.seed_min ? atomicAdd(&p.st[l].seed_rows, 1) : -1;
         } else {
             const int32_t b = atomicAdd(&p.st[l].ndirect, len);  // packed from the lane's slot_base
             for (int32_t q = 0; q < len; ++q) p.dlist[L.slot_base + b + q] = g + q;

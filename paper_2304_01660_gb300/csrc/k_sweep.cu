@@ -40,13 +40,18 @@ struct WarpSmem {
     float* tw;      // [2][kp + 32] series slices of this and the next chunk
     float4* colrec; // [2][32]      column records of this and the next chunk
     float* seed;    // [32]         top-row dot products of this chunk
+    float* tcseed;  // [2][32]      tensor-core top-row seeds of this and the next chunk
 };
 
-__device__ __forceinline__ size_t warp_smem_floats(int kp) { return size_t(kp) + 2 * (kp + 32) + 2 * 128 + 32; }
+__device__ __forceinline__ size_t warp_smem_floats(int kp) { return size_t(kp) + 2 * (kp + 32) + 2 * 128 + 32 + 64; }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
     const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc, int src_bytes) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -61,17 +66,23 @@ struct LaneView {
 
 // Start the asynchronous copy of chunk c0's series slice and column records
 // into buffer b (zero fill past the ends of T and of the windows).  T and
-// win are 16-byte aligned and c0 is a multiple of 32.
+// win are 16-byte aligned and c0 is a multiple of 32.  With tensor-core
+// seeds (tcs: the strip's seed row) the chunk's seeds replace the slice.
 __device__ __forceinline__ void issue_chunk(const LaneView& a, const WarpSmem& sm, int kps, int b, int64_t c0,
-                                            int kp, int lane) {
-    float* tw = sm.tw + b * (kps + 32);
-    for (int x = lane * 4; x < kp + 32; x += 128) {
-        const int64_t t = c0 + x;
-        const int64_t rem = a.n - t;
-        const int bytes = rem >= 4 ? 16 : (rem > 0 ? int(rem) * 4 : 0);
-        cp_async16(tw + x, bytes > 0 ? static_cast<const void*>(a.T + t) : static_cast<const void*>(a.T), bytes);
-    }
+                                            int kp, int lane, const float* tcs) {
     const int64_t j = c0 + lane;
+    if (tcs) {
+        cp_async4(sm.tcseed + b * 32 + lane, j < a.N ? static_cast<const void*>(tcs + j) : static_cast<const void*>(tcs),
+                  j < a.N ? 4 : 0);
+    } else {
+        float* tw = sm.tw + b * (kps + 32);
+        for (int x = lane * 4; x < kp + 32; x += 128) {
+            const int64_t t = c0 + x;
+            const int64_t rem = a.n - t;
+            const int bytes = rem >= 4 ? 16 : (rem > 0 ? int(rem) * 4 : 0);
+            cp_async16(tw + x, bytes > 0 ? static_cast<const void*>(a.T + t) : static_cast<const void*>(a.T), bytes);
+        }
+    }
     cp_async16(sm.colrec + b * 32 + lane, j < a.N ? static_cast<const void*>(a.win + j) : static_cast<const void*>(a.win),
                j < a.N ? 16 : 0);
     cp_async_commit();
@@ -179,7 +190,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
     const int kps = ((p.kpad_max + 127) / 128) * 128;  // smem stride (largest lane)
     float* base = smem + warp_smem_floats(kps) * wid;
     const WarpSmem sm{base, base + kps, reinterpret_cast<float4*>(base + kps + 2 * (kps + 32)),
-                      base + kps + 2 * (kps + 32) + 256};
+                      base + kps + 2 * (kps + 32) + 256, base + kps + 2 * (kps + 32) + 256 + 32};
     int64_t* strip_base = reinterpret_cast<int64_t*>(smem + warp_smem_floats(kps) * kWarpsPerCta);
     if (!REFINE) {
         for (int l = threadIdx.x; l < p.nl; l += blockDim.x) strip_base[l] = p.lanes[l].strip_base;
@@ -243,6 +254,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
         // rows start from directly computed dot products at column ja
         // (refine, and select pieces after the first)
         const bool seeded = REFINE || piece > 0;
+        // tensor-core seed row of a refine strip, if it has one
+        const float* tcs = nullptr;
+        if (REFINE && p.tc_seeds) {
+            const int32_t loc = p.strip_row[item % nref];
+            const LaneState& S = p.st[l];
+            if (loc >= 0 && loc < S.seed_eff) tcs = p.seeds + (int64_t(S.seed_base) + loc) * p.seed_stride;
+        }
         uint32_t* bits = Lg.bits;
         const int32_t* slot_of = Lg.slot_of;
         const int64_t i0 = s * H;
@@ -276,18 +294,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
         if (!__any_sync(kFull, alive)) continue;
 
         const int64_t cfirst = ja & ~int64_t(31);
-        issue_chunk(a, sm, kps, 0, cfirst, kp, lane);
+        issue_chunk(a, sm, kps, 0, cfirst, kp, lane, tcs);
 
         // Centred top-row window and its sum (FP32; the sum absorbs the
         // rounding of mu so the seed correction is exact to rounding).
-        const float mu_top = a.win[i0].w;
-        float part = 0.f;
-        for (int k = lane; k < kp; k += 32) {
-            const float v = (k < m) ? (a.T[i0 + k] - mu_top) : 0.f;
-            sm.ahat[k] = v;
-            part += v;
+        float suma = 0.f;
+        if (!tcs) {
+            const float mu_top = a.win[i0].w;
+            float part = 0.f;
+            for (int k = lane; k < kp; k += 32) {
+                const float v = (k < m) ? (a.T[i0 + k] - mu_top) : 0.f;
+                sm.ahat[k] = v;
+                part += v;
+            }
+            suma = warp_sum(part);
         }
-        const float suma = warp_sum(part);
         __syncwarp();
 
         float tmax[D];
@@ -303,7 +324,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
         for (int64_t c0 = cfirst; c0 < jb; c0 += 32, buf ^= 1) {
             cp_async_wait_all();
             __syncwarp();
-            if (c0 + 32 < jb) issue_chunk(a, sm, kps, buf ^ 1, c0 + 32, kp, lane);
+            if (c0 + 32 < jb) issue_chunk(a, sm, kps, buf ^ 1, c0 + 32, kp, lane, tcs);
             // state other warps may have changed, read early and used at the chunk end
             uint32_t gbits = 0, gdead = 0;
             if (!REFINE && r0 < N) gbits = __ldcg(&bits[wrd]);
@@ -312,7 +333,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
                 for (int d = 0; d < D; ++d)
                     if (((alive >> d) & 1u) && __ldcg(&p.dead[slot[d]])) gdead |= 1u << d;
             }
-            chunk_seeds(a, sm, kps, buf, c0, suma, kp, lane);
+            const float* seedv = tcs ? sm.tcseed + buf * 32 : sm.seed;
+            if (!tcs) chunk_seeds(a, sm, kps, buf, c0, suma, kp, lane);
             const float4* crb = sm.colrec + buf * 32;
             const int steps = int(min64(32, jb - c0));
             const int st0 = int(max64(0, ja - c0));
@@ -326,7 +348,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
             auto step = [&](int st, bool first_col, bool mask) {
                 const int64_t j = c0 + st;
                 const float4 cr = crb[st];
-                const float sd = sm.seed[st];
+                const float sd = seedv[st];
                 const float up = __shfl_up_sync(kFull, cov[D - 1], 1);
                 if (!first_col) {
 #pragma unroll
@@ -357,7 +379,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
                 for (int st = st0; st < steps; ++st) step(st, seeded && c0 + st == ja, masked);
             }
             if (lane == 0) {
-                seeds += 32;
+                if (!tcs) seeds += 32;
                 if (REFINE) pairs += uint64_t(rows) * uint64_t(steps - st0);
                 else
                     for (int st = st0; st < steps; ++st) {
@@ -414,7 +436,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
 
 size_t sweep_smem(const Pass& p) {
     const size_t kp = ((p.kpad_max + 127) / 128) * 128;
-    return sizeof(float) * (kp + 2 * (kp + 32) + 2 * 128 + 32) * kWarpsPerCta + sizeof(int64_t) * size_t(p.nl);
+    return sizeof(float) * (kp + 2 * (kp + 32) + 2 * 128 + 32 + 64) * kWarpsPerCta + sizeof(int64_t) * size_t(p.nl);
 }
 
 template <bool REFINE>

@@ -24,7 +24,10 @@ __global__ void k_round_cleanup(const Pass p) {
     for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < p.nslots; g += gridDim.x * blockDim.x) {
         const int l = p.slot_lane[g];
         const Lane& L = p.lanes[l];
-        if (g == L.slot_base) p.st[l].ndirect = 0;
+        if (g == L.slot_base) {
+            p.st[l].ndirect = 0;
+            p.st[l].seed_rows = 0;
+        }
         const int32_t w = p.slot_win[g];
         if (w < 0) continue;
         L.slot_of[w] = -1;

@@ -93,7 +93,10 @@ struct LaneState {
     int32_t count_final;   // range discords at the final r (finalize)
     uint32_t maxerr;       // enc_f32 of the largest |rho_fp32 - rho_fp64| seen
     int32_t ndirect;       // survivors of this refine round routed to the direct form
-    int32_t pad;
+    int32_t seed_rows;     // refine strips of this round asking for tensor-core seeds
+    int32_t seed_base;     // their first row in the seed buffer
+    int32_t seed_eff;      // rows granted (seed_rows clipped to the buffer)
+    uint32_t seed_eps;     // float bits: error bound of the tensor-core seeds (rho units)
 };
 
 // Everything a pass kernel needs, passed by value.
@@ -114,6 +117,8 @@ struct Pass {
     int32_t kpad_max;
     int32_t nchunks_max;   // 32-column chunks of the largest lane
     int32_t mixed;         // 1: direct refine on the tensor cores (k_refine_tc)
+    int32_t kpad_pass;     // largest kpad of this pass's lanes (kpad_max is the pool's stride)
+    int32_t pad5;
     int32_t* slot_lane;    // [slots] lane of each slot
     int32_t* slot_win;     // [slots] window of each slot, -1 for padding
     int32_t* route;        // [slots] 0 sweep, 1 direct, -1 none
@@ -127,6 +132,18 @@ struct Pass {
     float* cmax;           // [slots][nchunks_max] maximum rho per 32-column chunk
     int2* strips;          // (lane, strip) swept by refine
     int32_t* nref;
+    // tensor-core top-row seeds of refine strips (mixed precision)
+    int32_t tc_seeds;      // 1: strips with >= seed_min survivors take seeds from `seeds`
+    int32_t seed_min;
+    int32_t* strip_row;    // [slots] per refine strip: its lane-local seed row, -1 for none
+    float* topcen;         // [seed_cap][kpad_max] centred top-row windows
+    float* topsum;         // [seed_cap]
+    float* seeds;          // [seed_cap][seed_stride] cov(top row, j)
+    int64_t seed_stride;
+    int32_t seed_cap;      // rows in the seed buffer
+    int32_t pad4;
+    int4* seed_groups;     // (lane, first row, rows, -) per group of <= 32 rows of one lane
+    int32_t* seed_ngroups;
     int32_t* err;          // set to 1 by a kernel whose bounded wait gave up
     int32_t* work;         // [8] work counters, zeroed per launch group
     unsigned long long* pairs;  // [8] 0 select, 1 direct refine, 2 fp64, 3 select seeds,
@@ -149,7 +166,8 @@ __device__ __forceinline__ float eps_bound(int32_t m, const LaneState& s) {
     const float bmax = __uint_as_float(__ldcg(&s.ab[1]));
     const float rec = float(kStripH - 1) * (2.f + 6.f * amax * bmax);
     const float dir = 2.f * float(m + 4) * (1.f + 14.f * amax);
-    return 2.f * u * (rec + dir + 32.f);
+    // top-row seeds from the tensor cores carry their own bound (0 otherwise)
+    return 2.f * u * (rec + dir + 32.f) + __uint_as_float(__ldcg(&s.seed_eps));
 }
 __device__ __forceinline__ float rho_prune_of(const Lane& L, const LaneState& s) {
     return L.prune ? L.rho_thr + fmaxf(eps_bound(L.m, s), L.band) : kInf;
@@ -177,6 +195,8 @@ cudaError_t launch_plan(const Pass& p, cudaStream_t s);
 cudaError_t launch_refine_sweep(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_refine_direct(const Pass& p, int grid, cudaStream_t s);
 bool refine_tc_supported(const Pass& p);
+bool seed_tc_supported(const Pass& p);
+cudaError_t launch_seeds(const Pass& p, int sms, cudaStream_t s);
 cudaError_t launch_refine_tc(const Pass& p, int sms, cudaStream_t s);
 cudaError_t launch_recheck(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_round_cleanup(const Pass& p, cudaStream_t s);

@@ -21,7 +21,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NONFINITE", -3: "ERR_OOM", -4: "ERR_C
 NOALLOC_MAX_WINDOWS = 1 << 18
 PREC_FP32, PREC_MIXED = 0, 1
 KERNELS = ["stats", "select", "compact", "plan", "refine_sweep", "refine_direct", "recheck", "gather", "topk", "heat",
-           "other", "spare"]
+           "other", "seed_tc"]
 
 
 class PalmadError(RuntimeError):
@@ -42,7 +42,9 @@ class Options(ctypes.Structure):
         ("profile", ctypes.c_int32),
         ("pool_slots", ctypes.c_int32),
         ("direct_below", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("tc_seed_min", ctypes.c_int32),
+        ("seed_rows_max", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
 
@@ -64,6 +66,8 @@ class Stats(ctypes.Structure):
         ("sweep_flops", ctypes.c_double),
         ("launches", ctypes.c_int64 * 12),
         ("kernel_ms", ctypes.c_double * 12),
+        ("seed_pairs", ctypes.c_int64),
+        ("seed_flops", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:

@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 MIXED = 1
 ALL_TC = dict(precision=MIXED, direct_below=129)
+ALL_SEED = dict(precision=MIXED, tc_seed_min=1)   # every swept strip seeded on the tensor cores
 
 
 @pytest.mark.parametrize("name", list(SERIES))
@@ -97,3 +98,59 @@ def test_fp32_direct_form_matches_oracle(ctx, name):
         mp, _ = oracle.matrix_profile(T, m)
         for r in _thresholds(mp, (0.5, 0.99)):
             _check_drag(ctx, T, m, float(r), _opts(direct_below=129))
+
+
+@pytest.mark.parametrize("name", list(SERIES))
+@pytest.mark.parametrize("m", [8, 37, 100, 300])
+def test_tc_seeds_drag_matches_oracle(ctx, name, m):
+    """Tensor-core top-row seeds for every refine strip of the sweep."""
+    T = SERIES[name]()
+    if len(T) < 2 * m:
+        pytest.skip("series too short")
+    mp, _ = oracle.matrix_profile(T, m)
+    seeded = 0
+    for r in _thresholds(mp, (0.5, 0.9, 0.99, 1.0)):
+        _check_drag(ctx, T, m, float(r), _opts(**ALL_SEED))
+        seeded += ctx.palmad_get_stats()["seed_pairs"]
+    assert seeded > 0  # the tensor-core seeds did run
+
+
+@pytest.mark.parametrize("W", [0, 16])
+@pytest.mark.parametrize("name,minL,maxL,K,excl", [
+    ("rw3000", 10, 40, 2, True),
+    ("sine4000", 50, 70, 3, True),
+    ("flat2200", 16, 30, 1, False),
+])
+def test_tc_seeds_merlin_matches_oracle(ctx, W, name, minL, maxL, K, excl):
+    T = SERIES[name]()
+    got = ctx.palmad_find_discords(T, minL, maxL, K, _opts(exclusive_topk=int(excl), batch_lengths=W, **ALL_SEED),
+                                   heatmap=True)
+    assert ctx.palmad_get_stats()["seed_pairs"] > 0
+    _check_merlin(got, oracle.merlin(T, minL, maxL, K, excl, heatmap=True), heat=True)
+
+
+@pytest.mark.parametrize("cap", [1, 5, 40])
+def test_tc_seeds_row_cap_and_rounds(ctx, cap):
+    """Seed rows clipped to a small cap (the rest seed on the CUDA cores),
+    with many refine rounds and lanes of different lengths."""
+    series = [SERIES["rw3000"](), SERIES["sine4000"](), synth.random_walk(2600, 50)]
+    mins, maxs = [10, 40, 100], [30, 60, 140]
+    outs = ctx.palmad_find_discords_batch(series, mins, maxs, 2, _opts(batch_lengths=8, pool_slots=256,
+                                                                          seed_rows_max=cap, **ALL_SEED))
+    assert ctx.palmad_get_stats()["seed_pairs"] > 0
+    for T, a, b, o in zip(series, mins, maxs, outs):
+        _check_merlin(o, oracle.merlin(T, a, b, 2, True))
+
+
+def test_tc_seeds_equal_fp32_full_size(ctx):
+    """sine100k: tensor-core seeds (default and every strip) give the FP32
+    form's results exactly, and seeds are in fact computed."""
+    w = synth.workload("sine100k")
+    T = w.series[0]
+    args = (T, w.minL[0], w.maxL[0], w.topK)
+    a = ctx.palmad_find_discords(*args, _opts(batch_lengths=16), heatmap=True)
+    for o in (_opts(batch_lengths=16, precision=MIXED, tc_seed_min=16), _opts(batch_lengths=16, **ALL_SEED)):
+        b = ctx.palmad_find_discords(*args, o, heatmap=True)
+        for k in ("idx", "nn", "count", "r", "heatmap"):
+            np.testing.assert_array_equal(a[k], b[k])
+        assert ctx.palmad_get_stats()["seed_pairs"] > 0
