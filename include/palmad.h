@@ -187,6 +187,23 @@ palmad_status palmad_find_discords(palmad_ctx *ctx, const float *T, int64_t n, i
                                    int32_t topK, const palmad_options *opt, int64_t *out_idx,
                                    double *out_nndist, int64_t *out_count, double *out_r, float *out_heatmap);
 
+/*
+ * Resume a MERLIN run at length m0 (checkpoint / resume per length; the
+ * schedule of Algorithm 1 depends on earlier lengths only through their
+ * nnDist, Sec. 3.1).  The run started at length minL_sched; hist holds the
+ * schedule inputs of lengths m0 - h .. m0 - 1, h = min(5, m0 - minL_sched):
+ * per length, the nnDist of its K-th pick, or of its last pick when fewer,
+ * or 0 when none (row l of out_nndist gives it).  The outputs cover lengths
+ * m0..maxL exactly as rows m0 - minL_sched .. of the uninterrupted run; the
+ * heatmap is [(maxL - m0 + 1) * (n - m0 + 1)], the uninterrupted rows cut
+ * to that width.  Host pointers; other rules as palmad_find_discords, plus
+ * 3 <= minL_sched <= m0 and hist values finite and >= 0.
+ */
+palmad_status palmad_find_discords_resume(palmad_ctx *ctx, const float *T, int64_t n, int32_t minL_sched, int32_t m0,
+                                          int32_t maxL, int32_t topK, const palmad_options *opt, const double *hist,
+                                          int64_t *out_idx, double *out_nndist, int64_t *out_count, double *out_r,
+                                          float *out_heatmap);
+
 /* As palmad_find_discords, but T and every output are DEVICE pointers on
  * the context's device; the call is stream-ordered on the context's stream
  * and returns after the results are written. */
@@ -249,6 +266,27 @@ palmad_status palmad_drag(palmad_ctx *ctx, const float *T, int64_t n, int32_t m,
 palmad_status palmad_topk_profile_noalloc(const double *nn_dev, int64_t N, int32_t m, double r, int32_t K,
                                           int32_t exclusive, int64_t *out_idx_dev, double *out_nn_dev,
                                           int64_t *out_count_dev, void *cuda_stream);
+
+/*
+ * The most interesting discords across lengths (Eq. 11, Sec. 6), from a
+ * discord heatmap the caller holds on the device (the out_heatmap_dev of
+ * palmad_find_discords_device, Eq. 10).  No allocation, no context.
+ *   heat_dev       [L * W] float32, row l = length minL + l (device).
+ *   score_dev      [W] float32 out: interest of each index, the largest
+ *                  heatmap value over the lengths (device, caller-owned).
+ *   best_m_dev     [W] int32 out: the smallest length reaching it (device).
+ *   out_idx_dev    [K] int64 picks, -1 past the last one (device).
+ *   out_m_dev      [K] int32 their lengths, 0 past the last one (device).
+ *   out_score_dev  [K] float32 their interest, 0 past the last one (device).
+ * Picks are greedy by (interest desc, index asc) among indices of positive
+ * interest; with exclusive != 0 a pick's window [i, i + m) overlaps no
+ * earlier pick's window.  1 <= K <= 1024.  Asynchronous on cuda_stream
+ * (NULL: the default stream).  Errors: PALMAD_ERR_ARG, PALMAD_ERR_CUDA.
+ */
+palmad_status palmad_discord_interest(const float *heat_dev, int32_t L, int64_t W, int32_t minL, int32_t K,
+                                      int32_t exclusive, float *score_dev, int32_t *best_m_dev,
+                                      int64_t *out_idx_dev, int32_t *out_m_dev, float *out_score_dev,
+                                      void *cuda_stream);
 
 /* Counters of the most recent find/drag call on this context. */
 palmad_status palmad_get_stats(const palmad_ctx *ctx, palmad_stats *out);

@@ -143,6 +143,23 @@ def topk(idx, nn, m: int, K: int, exclusive: bool = True):
     return oi, on
 
 
+def interest(heat, minL: int, K: int, exclusive: bool = True):
+    """Eq. 11: per-index interest (largest heatmap value over the lengths)
+    and its length, and the greedy top-K interesting discords.  Returns a
+    dict with ``score`` [W], ``best_m`` [W], ``idx`` [K], ``m`` [K],
+    ``value`` [K] (-1 / 0 / 0 past the last pick)."""
+    heat = np.ascontiguousarray(heat, dtype=np.float32)
+    L, W = heat.shape
+    out = {"score": np.empty(W, dtype=np.float32), "best_m": np.empty(W, dtype=np.int32),
+           "idx": np.empty(K, dtype=np.int64), "m": np.empty(K, dtype=np.int32), "value": np.empty(K, dtype=np.float32)}
+    got = _load().oracle_interest(_p(heat, _f32p), L, W, minL, K, int(exclusive), _p(out["score"], _f32p),
+                                  _p(out["best_m"], _i32p), _p(out["idx"], _i64p), _p(out["m"], _i32p),
+                                  _p(out["value"], _f32p))
+    if got < 0:
+        raise ValueError(f"oracle_interest rc={got}")
+    return out
+
+
 def merlin(T, minL: int, maxL: int, K: int, exclusive: bool = True, heatmap: bool = False):
     """MERLIN (Algorithm 1) over lengths minL..maxL.  Returns a dict with
     ``idx`` [L,K], ``nn`` [L,K], ``count`` [L], ``r`` [L], ``calls`` [L] and,

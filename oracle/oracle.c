@@ -49,6 +49,12 @@
  *   R9  Heatmap (Eq. 10): row m, column i holds nnDist^2 / (2m) for the
  *       range discords at the final r of that length and 0 elsewhere; the
  *       row width is n - minL + 1.
+ *   R13 Discord interest (Eq. 11, Sec. 6): the interest of index i is the
+ *       largest heatmap value over the lengths, and its length the smallest
+ *       m reaching it.  The top-k interesting discords are taken greedily
+ *       by (interest desc, index asc) among indices of positive interest;
+ *       with `exclusive` set, a pick's window [i, i + m) must not overlap an
+ *       earlier pick's window.
  *
  * Parallelism: the brute-force nearest neighbour runs its rows in parallel
  * and DRAG phase 2 runs its candidates in parallel (each candidate sees the
@@ -371,6 +377,54 @@ int oracle_merlin(const float *T, int64_t n, int32_t minL, int32_t maxL, int32_t
     }
     free(b.idx); free(b.nn); free(sched);
     return rc;
+}
+
+/* ---------- discord interest across lengths (Eq. 11, reading R13) ---------- */
+
+/*
+ * heat: [L * W] row-major by length (row l is length minL + l).
+ * score / best_m: [W] per index, or NULL.  out_idx / out_m / out_score: [K]
+ * picks, -1 / 0 / 0 past the last one.  Returns the number of picks.
+ */
+int oracle_interest(const float *heat, int32_t L, int64_t W, int32_t minL, int32_t K, int exclusive, float *score,
+                    int32_t *best_m, int64_t *out_idx, int32_t *out_m, float *out_score) {
+    if (!heat || L < 1 || W < 1 || K < 1) return -1;
+    float *sc = (float *)malloc(sizeof(float) * (size_t)W);
+    int32_t *bm = (int32_t *)malloc(sizeof(int32_t) * (size_t)W);
+    if (!sc || !bm) { free(sc); free(bm); return -2; }
+    for (int64_t i = 0; i < W; ++i) {
+        float best = heat[i];
+        int32_t at = 0;
+        for (int32_t l = 1; l < L; ++l) {
+            const float v = heat[(int64_t)l * W + i];
+            if (v > best) { best = v; at = l; }
+        }
+        sc[i] = best;
+        bm[i] = minL + at;
+    }
+    int32_t got = 0;
+    for (; got < K; ++got) {
+        int64_t pick = -1;
+        for (int64_t i = 0; i < W; ++i) {
+            if (!(sc[i] > 0.0f)) continue;
+            if (pick >= 0 && !(sc[i] > sc[pick])) continue; /* ties keep the lower index */
+            int ok = 1;
+            for (int32_t g = 0; g < got && ok; ++g) {
+                if (out_idx[g] == i) ok = 0;
+                else if (exclusive && i < out_idx[g] + out_m[g] && out_idx[g] < i + bm[i]) ok = 0;
+            }
+            if (ok) pick = i;
+        }
+        if (pick < 0) break;
+        out_idx[got] = pick;
+        out_m[got] = bm[pick];
+        out_score[got] = sc[pick];
+    }
+    for (int32_t g = got; g < K; ++g) { out_idx[g] = -1; out_m[g] = 0; out_score[g] = 0.0f; }
+    if (score) memcpy(score, sc, sizeof(float) * (size_t)W);
+    if (best_m) memcpy(best_m, bm, sizeof(int32_t) * (size_t)W);
+    free(sc); free(bm);
+    return got;
 }
 
 int oracle_num_threads(void) {

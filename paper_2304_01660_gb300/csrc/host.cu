@@ -593,6 +593,11 @@ struct SeriesJob {
     int64_t hw = 0;
     int64_t* count_dev = nullptr;  // device [L] counts
     int32_t* init_flag = nullptr;  // device int for the non-finite check
+    // resumed run: length index minL - minL_sched of the schedule's own run
+    // (loff), and the schedule inputs of the lengths before minL (hist)
+    int32_t loff = 0;
+    int32_t minL_sched = 0;
+    std::vector<double> hist;
     // results
     std::vector<int64_t> idx;
     std::vector<double> nn, r_final;
@@ -614,7 +619,8 @@ struct SeriesJob {
     std::vector<std::vector<double>> wnn;
     int32_t rerun_l = -1;       // length awaiting a rerun result
     double rerun_r = 0.0;
-    std::vector<double> first_r;  // first try of each length (for the deficit)
+    std::vector<double> first_r;  // first try of each length (for the deficit), by schedule index
+    std::vector<double> rfin_v;   // final r of each length, by schedule index
 
     int set_of(int32_t li) const { return set0 + (W > 1 ? (li % W) : 0); }
     int32_t m_of(int32_t li) const { return minL + li; }
@@ -658,17 +664,17 @@ Lane make_lane(palmad_ctx* ctx, SeriesJob& s, int32_t li, double r, const palmad
 }
 
 // How far below its first try the schedule ended, recently (largest of the
-// last eight decided lengths).
+// last eight decided lengths; l0 and the arrays are schedule indices).
 double recent_deficit(const SeriesJob& s, int32_t l0) {
     double d = 0.0;
-    for (int32_t q = std::max(5, l0 - 8); q < l0; ++q) d = std::max(d, s.first_r[q] - s.r_final[q]);
+    for (int32_t q = std::max(5, l0 - 8); q < l0; ++q) d = std::max(d, s.first_r[q] - s.rfin_v[q]);
     return d;
 }
 
 // Speculative threshold for the window lengths: below the first try of the
 // schedule by about two decrements, 6%, or 1.5x the recent deficit,
 // whichever is largest (never below half the recent mean).
-double speculative_r(const SeriesJob& s, int32_t l0) {
+double speculative_r(const SeriesJob& s, int32_t l0) {  // l0: schedule index
     double mean = 0.0, var = 0.0;
     for (int q = 1; q <= 5; ++q) mean += s.sched[l0 - q];
     mean /= 5.0;
@@ -688,8 +694,9 @@ void accept_length(SeriesJob& s, int32_t li, double r, const LaneState& st, cons
         s.nn[size_t(li) * s.K + q] = ok ? pnn[q] : 0.0;
         got += ok;
     }
-    s.sched[li] = got > 0 ? s.nn[size_t(li) * s.K + got - 1] : 0.0;
+    s.sched[li + s.loff] = got > 0 ? s.nn[size_t(li) * s.K + got - 1] : 0.0;
     s.r_final[li] = r;
+    s.rfin_v[li + s.loff] = r;
     s.lstate[li] = st;
     PassLane f{};
     f.lane = make_lane(ctx, s, li, r, o);
@@ -716,18 +723,18 @@ void series_request(palmad_ctx* ctx, SeriesJob& s, std::vector<PassLane>& req, s
         push(s.rerun_l, s.rerun_r, false);
         return;
     }
-    if (s.W > 1 && s.l >= 5) {
+    if (s.W > 1 && s.l + s.loff >= 5) {
         s.wl0 = s.l;
         s.wn = std::min<int32_t>(s.W, s.L - s.l);
-        s.rspec.assign(s.wn, speculative_r(s, s.l));
+        s.rspec.assign(s.wn, speculative_r(s, s.l + s.loff));
         for (int w = 0; w < s.wn; ++w) push(s.wl0 + w, s.rspec[w], w + 1 < s.wn);
         s.phase = SeriesJob::kWindow;
         return;
     }
     if (!s.tr_started) {
-        s.tr.start(s.l, s.sched, s.minL);
+        s.tr.start(s.l + s.loff, s.sched, s.minL_sched);
         s.tr_started = true;
-        s.first_r[s.l] = s.tr.r;
+        s.first_r[s.l + s.loff] = s.tr.r;
     }
     push(s.l, s.tr.r, false);
     s.phase = SeriesJob::kPlain;
@@ -740,9 +747,9 @@ void series_replay(palmad_ctx* ctx, SeriesJob& s, std::vector<PassLane>& fin, co
     while (s.l < s.wl0 + s.wn) {
         const int w = s.l - s.wl0;
         if (!s.tr_started) {
-            s.tr.start(s.l, s.sched, s.minL);
+            s.tr.start(s.l + s.loff, s.sched, s.minL_sched);
             s.tr_started = true;
-            s.first_r[s.l] = s.tr.r;
+            s.first_r[s.l + s.loff] = s.tr.r;
         }
         const double rs = s.rspec[w];
         for (;;) {
@@ -751,7 +758,7 @@ void series_replay(palmad_ctx* ctx, SeriesJob& s, std::vector<PassLane>& fin, co
                 // the schedule needs r below this length's r': rerun it lower,
                 // by at least three decrements, 10% or 1.5x the recent deficit
                 const double step = s.tr.step > 0.0 ? s.tr.step : 0.01 * r;
-                const double drop = std::max({3.0 * step, 0.1 * r, 1.5 * recent_deficit(s, s.l)});
+                const double drop = std::max({3.0 * step, 0.1 * r, 1.5 * recent_deficit(s, s.l + s.loff)});
                 s.rerun_l = s.l;
                 s.rerun_r = r - drop;
                 if (s.rerun_r < 0.05 * r) s.rerun_r = 0.05 * r;  // stay clear of the r = 0 full profile
@@ -837,9 +844,12 @@ palmad_status run_jobs(palmad_ctx* ctx, std::vector<SeriesJob>& jobs, const palm
         s.idx.assign(size_t(s.L) * s.K, -1);
         s.nn.assign(size_t(s.L) * s.K, 0.0);
         s.r_final.assign(s.L, 0.0);
-        s.sched.assign(s.L, 0.0);
+        if (s.minL_sched == 0) s.minL_sched = s.minL;
+        s.sched.assign(s.loff + s.L, 0.0);
+        for (size_t q = 0; q < s.hist.size(); ++q) s.sched[s.loff - s.hist.size() + q] = s.hist[q];
         s.lstate.assign(s.L, LaneState{});
-        s.first_r.assign(s.L, 0.0);
+        s.first_r.assign(s.loff + s.L, 0.0);
+        s.rfin_v.assign(s.loff + s.L, 0.0);
     }
     // initial statistics (Eq. 4 at minL) and the non-finite check
     CKS(ensure(ctx, ctx->init_flags, jobs.size()));
@@ -1066,11 +1076,12 @@ palmad_status palmad_find_discords_device(palmad_ctx* ctx, const float* T_dev, i
     return st;
 }
 
-palmad_status palmad_find_discords(palmad_ctx* ctx, const float* T, int64_t n, int32_t minL, int32_t maxL,
-                                   int32_t topK, const palmad_options* opt, int64_t* out_idx, double* out_nndist,
-                                   int64_t* out_count, double* out_r, float* out_heatmap) {
-    CKS(check_args(ctx, n, minL, maxL, topK));
-    if (!T || !out_idx || !out_nndist) return fail(ctx, PALMAD_ERR_ARG, "null T or output pointer");
+// One host-pointer series, lengths minL..maxL; a resumed run passes the
+// schedule's own first length (minL_sched) and the schedule inputs of the
+// lengths just before minL.
+static palmad_status find_one(palmad_ctx* ctx, const float* T, int64_t n, int32_t minL, int32_t maxL, int32_t topK,
+                              const palmad_options* opt, int64_t* out_idx, double* out_nndist, int64_t* out_count,
+                              double* out_r, float* out_heatmap, int32_t minL_sched, const std::vector<double>& hist) {
     palmad_options o;
     CKS(read_options(ctx, opt, o));
     CKS(begin_call(ctx, o));
@@ -1100,6 +1111,9 @@ palmad_status palmad_find_discords(palmad_ctx* ctx, const float* T, int64_t n, i
     s.heat = out_heatmap ? heat.p : nullptr;
     s.hw = hw;
     s.count_dev = cnt.p;
+    s.minL_sched = minL_sched;
+    s.loff = minL - minL_sched;
+    s.hist = hist;
     palmad_status st = run_jobs(ctx, jobs, o);
     std::vector<int64_t> counts(L);
     if (st == PALMAD_OK) {
@@ -1121,6 +1135,29 @@ palmad_status palmad_find_discords(palmad_ctx* ctx, const float* T, int64_t n, i
     release(cnt);
     release(heat);
     return st;
+}
+
+palmad_status palmad_find_discords(palmad_ctx* ctx, const float* T, int64_t n, int32_t minL, int32_t maxL,
+                                   int32_t topK, const palmad_options* opt, int64_t* out_idx, double* out_nndist,
+                                   int64_t* out_count, double* out_r, float* out_heatmap) {
+    CKS(check_args(ctx, n, minL, maxL, topK));
+    if (!T || !out_idx || !out_nndist) return fail(ctx, PALMAD_ERR_ARG, "null T or output pointer");
+    return find_one(ctx, T, n, minL, maxL, topK, opt, out_idx, out_nndist, out_count, out_r, out_heatmap, minL, {});
+}
+
+palmad_status palmad_find_discords_resume(palmad_ctx* ctx, const float* T, int64_t n, int32_t minL_sched,
+                                          int32_t m0, int32_t maxL, int32_t topK, const palmad_options* opt,
+                                          const double* hist, int64_t* out_idx, double* out_nndist,
+                                          int64_t* out_count, double* out_r, float* out_heatmap) {
+    CKS(check_args(ctx, n, m0, maxL, topK));
+    if (minL_sched < 3 || m0 < minL_sched) return fail(ctx, PALMAD_ERR_ARG, "need 3 <= minL_sched <= m0");
+    if (!T || !out_idx || !out_nndist) return fail(ctx, PALMAD_ERR_ARG, "null T or output pointer");
+    const int32_t nh = std::min(5, m0 - minL_sched);
+    if (nh > 0 && !hist) return fail(ctx, PALMAD_ERR_ARG, "null schedule history");
+    std::vector<double> h(hist, hist + nh);
+    for (double v : h)
+        if (!(v >= 0.0) || !std::isfinite(v)) return fail(ctx, PALMAD_ERR_ARG, "schedule history must be finite and >= 0");
+    return find_one(ctx, T, n, m0, maxL, topK, opt, out_idx, out_nndist, out_count, out_r, out_heatmap, minL_sched, h);
 }
 
 palmad_status palmad_find_discords_batch(palmad_ctx* ctx, int32_t count, const float* const* T, const int64_t* n,

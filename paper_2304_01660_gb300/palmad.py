@@ -102,6 +102,9 @@ def load(path: str = LIB_PATH):
     lib.palmad_find_discords.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.POINTER(Options), _vp, _vp, _vp, _vp, _vp]
     lib.palmad_find_discords_device.argtypes = lib.palmad_find_discords.argtypes
+    lib.palmad_find_discords_resume.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Options), _vp, _vp,
+                                                _vp, _vp, _vp, _vp]
     lib.palmad_find_discords_batch.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_int32,
                                                ctypes.POINTER(Options), _vp, _vp, _vp, _vp]
     lib.palmad_drag.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
@@ -109,9 +112,12 @@ def load(path: str = LIB_PATH):
     lib.palmad_topk_profile_noalloc.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                 ctypes.c_int32, _vp, _vp, _vp, _vp]
     lib.palmad_measure_peak.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    lib.palmad_discord_interest.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
     for name in ("palmad_default_options", "palmad_create", "palmad_get_stats", "palmad_find_discords",
                  "palmad_find_discords_device", "palmad_find_discords_batch", "palmad_drag",
-                 "palmad_topk_profile_noalloc", "palmad_measure_peak"):
+                 "palmad_topk_profile_noalloc", "palmad_measure_peak", "palmad_discord_interest",
+                 "palmad_find_discords_resume"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -148,6 +154,38 @@ def palmad_topk_profile_noalloc(nn_dev, m: int, r: float, K: int, exclusive: boo
     if st != PALMAD_OK:
         raise PalmadError(st, "palmad_topk_profile_noalloc failed")
     return idx, nn, cnt
+
+
+def palmad_discord_interest(heat_dev, minL: int, K: int, exclusive: bool = True, stream=None) -> dict:
+    """Eq. 11 on a device heatmap (float32 CUDA tensor [L, W]): per-index
+    interest and length, and the top-K interesting discords.  Returns CUDA
+    tensors ``score`` [W], ``best_m`` [W], ``idx`` [K], ``m`` [K], ``value`` [K]."""
+    import torch
+    assert heat_dev.is_cuda and heat_dev.dtype == torch.float32 and heat_dev.is_contiguous() and heat_dev.dim() == 2
+    L, W = heat_dev.shape
+    dev = heat_dev.device
+    out = {"score": torch.empty(W, dtype=torch.float32, device=dev), "best_m": torch.empty(W, dtype=torch.int32, device=dev),
+           "idx": torch.empty(K, dtype=torch.int64, device=dev), "m": torch.empty(K, dtype=torch.int32, device=dev),
+           "value": torch.empty(K, dtype=torch.float32, device=dev)}
+    s = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    st = load().palmad_discord_interest(heat_dev.data_ptr(), L, W, minL, K, int(bool(exclusive)),
+                                        out["score"].data_ptr(), out["best_m"].data_ptr(), out["idx"].data_ptr(),
+                                        out["m"].data_ptr(), out["value"].data_ptr(), s)
+    if st != PALMAD_OK:
+        raise PalmadError(st, "palmad_discord_interest failed")
+    return out
+
+
+def schedule_inputs(idx, nn) -> np.ndarray:
+    """Per length, the value the schedule of Algorithm 1 carries to the next
+    lengths: nnDist of the K-th pick, of the last pick when fewer, 0 when
+    none (idx / nn: [L, K] results).  A checkpoint at length m0 of a run
+    that started at minL is schedule_inputs(...)[max(0, l0 - 5):l0],
+    l0 = m0 - minL."""
+    idx = np.asarray(idx)
+    nn = np.asarray(nn, dtype=np.float64)
+    got = (idx >= 0).sum(axis=1)
+    return np.where(got > 0, nn[np.arange(len(nn)), np.maximum(got - 1, 0)], 0.0)
 
 
 PEAK_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
@@ -222,6 +260,26 @@ class Context:
             _ptr(idx), _ptr(nn), _ptr(cnt), _ptr(rr), _ptr(heat)))
         out = {"idx": idx, "nn": nn, "count": cnt, "r": rr}
         if heat is not None:
+            out["heatmap"] = heat
+        return out
+
+    def palmad_find_discords_resume(self, T, minL_sched: int, m0: int, maxL: int, topK: int, hist,
+                                    options: Options | None = None, heatmap: bool = False) -> dict:
+        """Lengths m0..maxL of a MERLIN run that started at minL_sched, from
+        the schedule inputs of the lengths before m0 (see schedule_inputs)."""
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        L = maxL - m0 + 1
+        h = np.ascontiguousarray(hist, dtype=np.float64)
+        idx = np.empty((L, topK), dtype=np.int64)
+        nn = np.empty((L, topK), dtype=np.float64)
+        cnt = np.empty(L, dtype=np.int64)
+        rr = np.empty(L, dtype=np.float64)
+        heat = np.empty((L, len(T) - m0 + 1), dtype=np.float32) if heatmap else None
+        self._check(self._lib.palmad_find_discords_resume(
+            self._h, _ptr(T), len(T), minL_sched, m0, maxL, topK, ctypes.byref(options) if options else None,
+            _ptr(h) if len(h) else None, _ptr(idx), _ptr(nn), _ptr(cnt), _ptr(rr), _ptr(heat)))
+        out = {"idx": idx, "nn": nn, "count": cnt, "r": rr}
+        if heatmap:
             out["heatmap"] = heat
         return out
 

@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -81,3 +83,10 @@ def test_create_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p()
     assert lib.palmad_create(ctypes.byref(h), 0, None) != 0
     assert not h.value
+
+
+def test_schedule_inputs_reads_the_kth_or_last_pick():
+    idx = np.array([[4, 9, 2], [4, 9, -1], [-1, -1, -1]])
+    nn = np.array([[3.0, 2.5, 2.0], [3.0, 2.5, 0.0], [0.0, 0.0, 0.0]])
+    from paper_2304_01660_gb300 import palmad
+    assert palmad.schedule_inputs(idx, nn).tolist() == [2.0, 2.5, 0.0]

@@ -310,3 +310,67 @@ def test_golden_fixtures_reproduce():
         idx, nn = oracle.drag(T, case["m"], case["r"])
         assert idx.tolist() == case["idx"]
         np.testing.assert_allclose(nn, case["nn"], rtol=1e-12)
+
+
+# ------------------------------------------------------------ Eq. 11 interest
+
+def _sparse_heat(L, W, seed, density=0.05):
+    rng = np.random.default_rng(seed)
+    h = np.where(rng.random((L, W)) < density, rng.random((L, W)), 0.0).astype(np.float32)
+    h[:, 5] = 0.25   # equal along m: the smallest length wins the tie
+    h[:, 9] = 0.0
+    h[2, 9] = h[4, 9] = 0.75
+    return h
+
+
+def test_interest_is_columnwise_max_with_first_length():
+    """Eq. 11 per index reduces to numpy's column max and first argmax."""
+    h = _sparse_heat(7, 300, 1)
+    got = oracle.interest(h, 40, 3)
+    np.testing.assert_array_equal(got["score"], h.max(axis=0))
+    np.testing.assert_array_equal(got["best_m"], 40 + h.argmax(axis=0))
+    assert got["best_m"][5] == 40 and got["best_m"][9] == 42
+
+
+def test_interest_plain_topk_is_a_sort():
+    """Without the overlap rule the picks are the K largest positive scores,
+    ties to the lower index (numpy lexsort)."""
+    h = _sparse_heat(5, 400, 2)
+    s = h.max(axis=0)
+    order = np.lexsort((np.arange(len(s)), -s))
+    order = [i for i in order if s[i] > 0][:25]
+    got = oracle.interest(h, 10, 25, exclusive=False)
+    np.testing.assert_array_equal(got["idx"], order)
+    np.testing.assert_array_equal(got["value"], s[order])
+
+
+def test_interest_exclusive_hand_example():
+    h = np.zeros((3, 40), np.float32)
+    h[0, 10] = 0.9                 # length 20: window [10, 30)
+    h[2, 28] = 0.8                 # length 22: [28, 50) overlaps [10, 30): skipped
+    h[1, 31] = 0.7                 # length 21: [31, 52) clear of [10, 30)
+    h[0, 0] = 0.6                  # length 20: [0, 20) overlaps [10, 30): skipped
+    got = oracle.interest(h, 20, 4)
+    assert got["idx"].tolist() == [10, 31, -1, -1]
+    assert got["m"].tolist() == [20, 21, 0, 0]
+    got = oracle.interest(h, 20, 4, exclusive=False)
+    assert got["idx"].tolist() == [10, 28, 31, 0]
+
+
+def test_interest_empty_heatmap():
+    got = oracle.interest(np.zeros((4, 50), np.float32), 8, 2)
+    assert got["idx"].tolist() == [-1, -1] and got["value"].tolist() == [0.0, 0.0]
+
+
+def test_interest_top1_is_a_per_length_top1():
+    """The most interesting discord (Eq. 11) is the per-length top-1 discord
+    whose nnDist^2 / (2m) (Eq. 10) is largest."""
+    T = synth.random_walk(1500, 3)
+    minL, maxL = 20, 27
+    res = oracle.merlin(T, minL, maxL, 1, True, heatmap=True)
+    got = oracle.interest(res["heatmap"], minL, 1)
+    ms = np.arange(minL, maxL + 1)
+    val = (res["nn"][:, 0] ** 2 / (2 * ms)).astype(np.float32)
+    l = int(np.argmax(val))
+    assert got["idx"][0] == res["idx"][l, 0]
+    assert got["value"][0] == val[l]
