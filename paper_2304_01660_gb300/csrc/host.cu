@@ -101,6 +101,7 @@ struct palmad_ctx {
     DBuf<int4> seed_groups;
     bool sets_dirty = false;       // a pass stopped early: slot maps may not be clean
     DBuf<float> acen, asum, cmax;
+    DBuf<uint32_t> cmax2;
     DBuf<uint32_t> gmax;
     DBuf<unsigned long long> nn2;
     DBuf<int2> strips;
@@ -313,7 +314,8 @@ palmad_status ensure_pool(palmad_ctx* ctx, int32_t kpad, int32_t nchunks) {
     if (ctx->pool > 0 && kpad <= ctx->pool_kpad && nchunks <= ctx->pool_nchunks) return PALMAD_OK;
     kpad = std::max(kpad, ctx->pool_kpad);
     nchunks = std::max(nchunks, ctx->pool_nchunks);
-    int64_t slots = kPoolBytes / (int64_t(sizeof(float)) * (nchunks + kpad));
+    const int64_t ncoarse = (int64_t(nchunks) * 32 + kCoarse - 1) / kCoarse;
+    int64_t slots = kPoolBytes / (int64_t(sizeof(float)) * (nchunks + ncoarse + kpad));
     slots = std::min<int64_t>(slots, 1 << 17);
     slots = std::max<int64_t>(64, (slots / 64) * 64);
     CKS(ensure(ctx, ctx->slot_lane, slots)); CKS(ensure(ctx, ctx->slot_win, slots)); CKS(ensure(ctx, ctx->route, slots));
@@ -322,6 +324,7 @@ palmad_status ensure_pool(palmad_ctx* ctx, int32_t kpad, int32_t nchunks) {
     CKS(ensure(ctx, ctx->nn2, slots));
     CKS(ensure(ctx, ctx->acen, size_t(slots) * kpad));
     CKS(ensure(ctx, ctx->cmax, size_t(slots) * nchunks));
+    CKS(ensure(ctx, ctx->cmax2, size_t(slots) * ncoarse));
     CKS(ensure(ctx, ctx->strips, size_t(slots))); CKS(ensure(ctx, ctx->strip_row, size_t(slots)));
     ctx->pool = int32_t(slots);
     ctx->pool_kpad = kpad;
@@ -337,6 +340,7 @@ Pass base_pass(palmad_ctx* ctx, int nl, int K, bool exclusive, const palmad_opti
     p.K = K;
     p.exclusive = exclusive ? 1 : 0;
     p.seg = kRefineSeg;
+    static_assert(kRefineSeg == kCoarse, "a refine segment is one coarse block of the chunk maxima");
     p.cap = o.select_cap > 0 ? o.select_cap : kDefaultCap;
     p.slot_lane = ctx->slot_lane.p;
     p.slot_win = ctx->slot_win.p;
@@ -349,6 +353,7 @@ Pass base_pass(palmad_ctx* ctx, int nl, int K, bool exclusive, const palmad_opti
     p.dead = ctx->dead.p;
     p.nn2 = ctx->nn2.p;
     p.cmax = ctx->cmax.p;
+    p.cmax2 = ctx->cmax2.p;
     p.strips = ctx->strips.p;
     p.nref = &ctx->small.p->nref;
     p.work = ctx->small.p->work;
@@ -398,6 +403,7 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     p.kpad_max = ctx->pool_kpad;
     p.kpad_pass = kpad_max;
     p.nchunks_max = ctx->pool_nchunks;
+    p.ncoarse_max = int32_t((int64_t(ctx->pool_nchunks) * 32 + kCoarse - 1) / kCoarse);
     p.mixed = (o.precision == PALMAD_PREC_MIXED && refine_tc_supported(p)) ? 1 : 0;
     p.direct_below = o.direct_below;
     p.strip_row = ctx->strip_row.p;
@@ -999,7 +1005,7 @@ void palmad_destroy(palmad_ctx* ctx) {
     release(ctx->lanes); release(ctx->st); release(ctx->chain); release(ctx->small);
     release(ctx->pidx); release(ctx->pnn);
     release(ctx->slot_lane); release(ctx->slot_win); release(ctx->route); release(ctx->dlist); release(ctx->dgroups); release(ctx->dead);
-    release(ctx->acen); release(ctx->asum); release(ctx->cmax); release(ctx->gmax); release(ctx->nn2);
+    release(ctx->acen); release(ctx->asum); release(ctx->cmax); release(ctx->cmax2); release(ctx->gmax); release(ctx->nn2);
     release(ctx->strips); release(ctx->init_flags);
     release(ctx->strip_row); release(ctx->topcen); release(ctx->topsum); release(ctx->seeds); release(ctx->seed_groups);
     if (ctx->h_lanes) cudaFreeHost(ctx->h_lanes);

@@ -172,6 +172,8 @@ __global__ void k_prep(const Pass p) {
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
         if (lane == 0) p.asum[g] = part;
+        if (p.route[g] == 1)  // the direct forms raise these with atomicMax; enc_f32 order: 0 is lowest
+            for (int k = lane; k < p.ncoarse_max; k += 32) p.cmax2[g * p.ncoarse_max + k] = 0u;
     }
 }
 
@@ -302,7 +304,10 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
 #pragma unroll
             for (int o = 4; o <= 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
             if (lane == 0 && sok) {
-                if (mx > -kInf) atomicMax(&p.gmax[g], enc_f32(mx));
+                if (mx > -kInf) {
+                    atomicMax(&p.gmax[g], enc_f32(mx));
+                    atomicMax(&p.cmax2[g * p.ncoarse_max + (j0 / kCoarse)], enc_f32(mx));  // tile inside one block
+                }
                 if (mx > rho_prune) p.dead[g] = 1;
             }
         }
@@ -324,7 +329,7 @@ constexpr int kRecheckCand = 512;
 constexpr int kRecheckWin = 1024;   // survivor windows up to this length use shared memory
 
 __global__ void __launch_bounds__(256) k_recheck(const Pass p) {
-    __shared__ int32_t flagged[256];
+    __shared__ int32_t flagged[256 * (kCoarse / 32)];
     __shared__ int32_t cand[kRecheckCand];
     __shared__ float candr[kRecheckCand];
     __shared__ double zc[kRecheckWin];
@@ -359,12 +364,20 @@ __global__ void __launch_bounds__(256) k_recheck(const Pass p) {
             for (int k = threadIdx.x; k < m; k += blockDim.x) zc[k] = (double(T[c + k]) - muc) * ic;
         const float* arow = p.acen + g * int64_t(p.kpad_max);
         const float* cm = p.cmax + g * int64_t(p.nchunks_max);
+        const uint32_t* c2 = p.cmax2 + g * int64_t(p.ncoarse_max);
         const int32_t nchunks = int32_t((N + 31) / 32);
-        for (int32_t cb = 0; cb < nchunks; cb += 256) {
+        const int32_t ncoarse = int32_t((N + kCoarse - 1) / kCoarse);
+        const uint32_t thr_enc = enc_f32(thr);
+        // coarse blocks first (one per thread), then their chunks
+        for (int32_t cb = 0; cb < ncoarse; cb += 256) {
             if (threadIdx.x == 0) nflag = 0;
             __syncthreads();
-            const int32_t q = cb + threadIdx.x;
-            if (q < nchunks && cm[q] >= thr) flagged[atomicAdd(&nflag, 1)] = q;
+            const int32_t q2 = cb + threadIdx.x;
+            if (q2 < ncoarse && c2[q2] >= thr_enc) {
+                const int32_t qe = min(nchunks, (q2 + 1) * (kCoarse / 32));
+                for (int32_t q = q2 * (kCoarse / 32); q < qe; ++q)
+                    if (cm[q] >= thr) flagged[atomicAdd(&nflag, 1)] = q;
+            }
             __syncthreads();
             const int nf = nflag;
             // flagged chunks 8 at a time (one per warp), candidates per batch

@@ -70,7 +70,7 @@ __host__ __device__ inline TcLayout tc_layout(int kp, int ns) {
     t.off_c = t.off_t + size_t(tc_span(kp)) * 4;  // column records (inv, mu)
     t.off_misc = t.off_c + size_t(kTcTiles * kTcM) * 8;
     // misc: survivor records (float4), slots, lower-bound maxima; mbar[2]; tmem slot; flag
-    t.total = t.off_misc + size_t(ns) * (16 + 4 + 4) + 64;
+    t.total = t.off_misc + size_t(ns) * (16 + 4 + 4 + 8) + 64;
     return t;
 }
 
@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
     float4* s_rec = reinterpret_cast<float4*>(smem + lay.off_misc);  // inv, sum of a, exclusion start bits, -
     int32_t* s_slot = reinterpret_cast<int32_t*>(s_rec + NS);
     uint32_t* s_lo = reinterpret_cast<uint32_t*>(s_slot + NS);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(s_lo + NS);  // 8-byte aligned: off_misc and NS*24 are
+    uint32_t* s_c2 = s_lo + NS;  // [2][NS] coarse-block maxima of the item (enc_f32)
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(s_c2 + 2 * NS);  // 8-byte aligned: off_misc and NS*32 are
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(mbar + 2);
     int* s_flag = reinterpret_cast<int*>(s_tmem + 1);           // a survivor of the item is alive
 
@@ -152,6 +153,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
             // columns w-m+1 .. w+m-1 overlap the survivor (no non-self match)
             s_rec[tid] = make_float4(inv, suma, __int_as_float(w - m + 1), 0.f);
             s_lo[tid] = 0u;  // enc_f32 order: 0 is below every float
+            s_c2[tid] = 0u;
+            s_c2[NS + tid] = 0u;
         }
         __syncthreads();
         if (!s_flag[0]) {
@@ -257,6 +260,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
                     const int32_t g = s_slot[s];
                     const float lo = keep - epsmax;
                     p.cmax[int64_t(g) * p.nchunks_max + chunk] = keep + epsmax;
+                    atomicMax(&s_c2[(t * kTcM) / kCoarse * NS + s], enc_f32(keep + epsmax));
                     if (lo > -kInf) atomicMax(&s_lo[s], enc_f32(lo));
                     if (lo > rp) p.dead[g] = 1;
                 }
@@ -312,7 +316,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
             if (tid == 0) atomicExch(p.err, 1);
             break;
         }
-        if (tid < nd && s_lo[tid]) atomicMax(&p.gmax[s_slot[tid]], s_lo[tid]);
+        if (tid < nd) {
+            if (s_lo[tid]) atomicMax(&p.gmax[s_slot[tid]], s_lo[tid]);
+            // the item's columns are whole coarse blocks (jstart is a multiple of 1024)
+            for (int b2 = 0; b2 < (kTcM * kTcTiles) / kCoarse; ++b2)
+                if (jstart + int64_t(b2) * kCoarse < N)
+                    p.cmax2[int64_t(s_slot[tid]) * p.ncoarse_max + jstart / kCoarse + b2] = s_c2[b2 * NS + tid];
+        }
         __syncthreads();
     }
     fence_before();

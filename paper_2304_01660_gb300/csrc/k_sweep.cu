@@ -425,9 +425,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(con
         cp_async_wait_all();  // no copy may land in a buffer the next item reuses
         __syncwarp();
         if (REFINE) {
+            // the segment is one coarse block: its maximum is this row's tmax
+            const int64_t qb = ja / kCoarse;
 #pragma unroll
             for (int d = 0; d < D; ++d)
-                if (slot[d] >= 0 && tmax[d] > -kInf) atomicMax(&p.gmax[slot[d]], enc_f32(tmax[d]));
+                if (slot[d] >= 0) {
+                    p.cmax2[int64_t(slot[d]) * p.ncoarse_max + qb] = enc_f32(tmax[d]);
+                    if (tmax[d] > -kInf) atomicMax(&p.gmax[slot[d]], enc_f32(tmax[d]));
+                }
         }
     }
     if (lane == 0 && pairs) atomicAdd(p.pairs + (REFINE ? 4 : 0), pairs);
