@@ -39,7 +39,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x ma
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per launch of a kernel from an ncu capture of the
 # current kernel source (profiles/); None once the kernel changes.
-TRAFFIC_PER_LAUNCH: dict[str, float | None] = {}
+TRAFFIC_PER_LAUNCH: dict[str, float | None] = {
+    "refine_sweep": 2.078464e6 + 1.28e3,  # profiles/k_sweep_sine100k.md
+}
 
 
 def _peaks():
