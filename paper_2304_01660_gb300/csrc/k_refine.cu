@@ -317,31 +317,32 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
 
 // -------------------------------------------------------- FP64 re-check
 
-__device__ __forceinline__ bool is_flat64(double mu, double sd) { return sd <= kFlatRel * fabs(mu); }
+// sigma <= 2^-22 |mu|, compared squared, exactly as the statistics kernel
+// decides it (a variance left slightly negative counts as flat)
+__device__ __forceinline__ bool is_flat_var(double mu, double var) {
+    const double fl = kFlatRel * mu;
+    return var <= fl * fl;
+}
 
-// One CTA per live survivor slot (persistent): threads recompute the FP32
-// rho of every column in a flagged 32-column chunk; the columns within 2 eps
-// of the FP32 maximum go to a shared candidate list, and each warp then
-// evaluates one candidate's FP64 distance with the m terms split over its
-// lanes (the survivor's z-normalised FP64 window is staged once in shared
-// memory).
-constexpr int kRecheckCand = 512;
-constexpr int kRecheckWin = 1024;   // survivor windows up to this length use shared memory
+// One warp per live survivor slot (persistent, no block barriers).  The
+// warp scans the survivor's coarse maxima, then the chunk maxima of the
+// coarse blocks that can hold its nearest neighbour, recomputes the FP32 rho
+// of each flagged 32-column chunk (a lane per column), and evaluates every
+// column within 2 eps of the FP32 maximum in FP64 with the m terms split
+// over the lanes; the survivor's z-normalised FP64 window is staged once in
+// the warp's shared memory.
+constexpr int kRecheckWarps = 8;
+constexpr int kRecheckWin = 512;    // survivor windows up to this length use shared memory
 
-__global__ void __launch_bounds__(256) k_recheck(const Pass p) {
-    __shared__ int32_t flagged[256 * (kCoarse / 32)];
-    __shared__ int32_t cand[kRecheckCand];
-    __shared__ float candr[kRecheckCand];
-    __shared__ double zc[kRecheckWin];
-    __shared__ int nflag, ncand;
-    __shared__ int64_t g_s;
+__global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
+    __shared__ double zc_all[kRecheckWarps][kRecheckWin];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double* zc = zc_all[wid];
     unsigned long long fp64 = 0;
     for (;;) {
-        if (threadIdx.x == 0) g_s = atomicAdd(p.work + 3, 1);
-        __syncthreads();
-        const int64_t g = g_s;
-        __syncthreads();
+        int64_t g = 0;
+        if (lane == 0) g = atomicAdd(p.work + 3, 1);
+        g = __shfl_sync(kFull, g, 0);
         if (g >= p.nslots) break;
         const int32_t c = p.slot_win[g];
         if (c < 0 || __ldcg(&p.dead[g])) continue;
@@ -354,82 +355,76 @@ __global__ void __launch_bounds__(256) k_recheck(const Pass p) {
         const WinRec* win = L.win;
         const float gm = dec_f32(__ldcg(&p.gmax[g]));
         const float thr = gm - 2.f * eps_bound(m, S);
+        const uint32_t thr_enc = enc_f32(thr);
         const bool has_flat = (S.flags & 2) != 0;
         const float invc = win[c].z;
-        const double muc = L.mu[c], sdc = sqrt(L.var[c]);
-        const bool flatc = is_flat64(muc, sdc);
-        const double ic = flatc ? 0.0 : 1.0 / sdc;
+        const double muc = L.mu[c], varc = L.var[c];
+        const bool flatc = is_flat_var(muc, varc);
+        const double ic = flatc ? 0.0 : 1.0 / sqrt(varc);
         const bool zc_smem = m <= kRecheckWin;
         if (zc_smem)
-            for (int k = threadIdx.x; k < m; k += blockDim.x) zc[k] = (double(T[c + k]) - muc) * ic;
+            for (int k = lane; k < m; k += 32) zc[k] = (double(T[c + k]) - muc) * ic;
+        __syncwarp();
         const float* arow = p.acen + g * int64_t(p.kpad_max);
         const float* cm = p.cmax + g * int64_t(p.nchunks_max);
         const uint32_t* c2 = p.cmax2 + g * int64_t(p.ncoarse_max);
         const int32_t nchunks = int32_t((N + 31) / 32);
         const int32_t ncoarse = int32_t((N + kCoarse - 1) / kCoarse);
-        const uint32_t thr_enc = enc_f32(thr);
-        // coarse blocks first (one per thread), then their chunks
-        for (int32_t cb = 0; cb < ncoarse; cb += 256) {
-            if (threadIdx.x == 0) nflag = 0;
-            __syncthreads();
-            const int32_t q2 = cb + threadIdx.x;
-            if (q2 < ncoarse && c2[q2] >= thr_enc) {
-                const int32_t qe = min(nchunks, (q2 + 1) * (kCoarse / 32));
-                for (int32_t q = q2 * (kCoarse / 32); q < qe; ++q)
-                    if (cm[q] >= thr) flagged[atomicAdd(&nflag, 1)] = q;
-            }
-            __syncthreads();
-            const int nf = nflag;
-            // flagged chunks 8 at a time (one per warp), candidates per batch
-            for (int f0 = 0; f0 < nf; f0 += 8) {
-                if (threadIdx.x == 0) ncand = 0;
-                __syncthreads();
-                const int f = f0 + wid;
-                if (f < nf) {
-                    const int64_t j = int64_t(flagged[f]) * 32 + lane;
+        for (int32_t cb = 0; cb < ncoarse; cb += 32) {
+            const int32_t q2l = cb + lane;
+            uint32_t bq2 = __ballot_sync(kFull, q2l < ncoarse && c2[q2l] >= thr_enc);
+            while (bq2) {
+                const int32_t q2 = cb + __ffs(bq2) - 1;
+                bq2 &= bq2 - 1;
+                // chunks of the coarse block (16 of them) above the threshold
+                const int32_t q = q2 * (kCoarse / 32) + lane;
+                uint32_t bq = __ballot_sync(kFull, lane < kCoarse / 32 && q < nchunks && cm[q] >= thr);
+                while (bq) {
+                    const int32_t qq = q2 * (kCoarse / 32) + __ffs(bq) - 1;
+                    bq &= bq - 1;
+                    // FP32 rho of the chunk's columns, one per lane
+                    const int64_t j = int64_t(qq) * 32 + lane;
+                    float rho32 = -kInf;
                     if (j < N && (j - c >= m || c - j >= m)) {
                         const float4 rj = win[j];
                         float acc = 0.f;
                         for (int k = 0; k < m; ++k) acc = fmaf(arow[k], T[j + k] - rj.w, acc);
-                        float rho32 = acc * invc * rj.z;
+                        rho32 = acc * invc * rj.z;
                         if (has_flat && (invc == 0.f || rj.z == 0.f)) rho32 = (invc == 0.f && rj.z == 0.f) ? 1.f : 0.f;
-                        if (rho32 >= thr) {
-                            const int at = atomicAdd(&ncand, 1);  // <= 256 per batch
-                            cand[at] = int32_t(j);
-                            candr[at] = rho32;
-                        }
                     }
-                }
-                __syncthreads();
-                const int nc = ncand;
-                for (int e = wid; e < nc; e += 8) {
-                    const int64_t j = cand[e];
-                    const double muj = L.mu[j], sdj = sqrt(L.var[j]);
-                    const bool flatj = is_flat64(muj, sdj);
-                    double d2 = 0.0;
-                    if (flatc && flatj) d2 = 0.0;
-                    else if (flatc || flatj) d2 = 2.0 * m;
-                    else {
-                        const double ij = 1.0 / sdj;
-                        for (int k = lane; k < m; k += 32) {
-                            const double zck = zc_smem ? zc[k] : (double(T[c + k]) - muc) * ic;
-                            const double x = zck - (double(T[j + k]) - muj) * ij;
-                            d2 = fma(x, x, d2);
-                        }
+                    uint32_t bc = __ballot_sync(kFull, rho32 >= thr);
+                    while (bc) {
+                        const int cl = __ffs(bc) - 1;
+                        bc &= bc - 1;
+                        const int64_t jc = int64_t(qq) * 32 + cl;
+                        const float rc32 = __shfl_sync(kFull, rho32, cl);
+                        const double muj = L.mu[jc], varj = L.var[jc];
+                        const bool flatj = is_flat_var(muj, varj);
+                        double d2 = 0.0;
+                        if (flatc && flatj) d2 = 0.0;
+                        else if (flatc || flatj) d2 = 2.0 * m;
+                        else {
+                            const double ij = 1.0 / sqrt(varj);
+                            for (int k = lane; k < m; k += 32) {
+                                const double zck = zc_smem ? zc[k] : (double(T[c + k]) - muc) * ic;
+                                const double x = zck - (double(T[jc + k]) - muj) * ij;
+                                d2 = fma(x, x, d2);
+                            }
 #pragma unroll
-                        for (int o = 16; o >= 1; o >>= 1) d2 += __shfl_xor_sync(kFull, d2, o);
-                    }
-                    if (lane == 0) {
-                        atomicMin(&p.nn2[g], static_cast<unsigned long long>(__double_as_longlong(d2)));
-                        atomicMax(&S.maxerr, enc_f32(fabsf(candr[e] - float(1.0 - d2 / (2.0 * m)))));
-                        ++fp64;
+                            for (int o = 16; o >= 1; o >>= 1) d2 += __shfl_xor_sync(kFull, d2, o);
+                        }
+                        if (lane == 0) {
+                            atomicMin(&p.nn2[g], static_cast<unsigned long long>(__double_as_longlong(d2)));
+                            atomicMax(&S.maxerr, enc_f32(fabsf(rc32 - float(1.0 - d2 / (2.0 * m)))));
+                            ++fp64;
+                        }
                     }
                 }
-                __syncthreads();
             }
         }
+        __syncwarp();
     }
-    if (fp64) atomicAdd(p.pairs + 2, fp64);
+    if (lane == 0 && fp64) atomicAdd(p.pairs + 2, fp64);
 }
 
 }  // namespace
@@ -460,7 +455,7 @@ cudaError_t launch_refine_direct(const Pass& p, int grid, cudaStream_t s) {
 
 cudaError_t launch_recheck(const Pass& p, int grid, cudaStream_t s) {
     if (p.nslots <= 0) return cudaSuccess;
-    k_recheck<<<grid, 256, 0, s>>>(p);
+    k_recheck<<<grid, kRecheckWarps * 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -60,10 +60,11 @@ __global__ void k_stats_init(const float* __restrict__ T, int64_t n, int32_t m, 
     if (bad) atomicOr(flags, 1);
 }
 
-// New (mu, var) of window i at length m from its values at m-1 (Eq. 7-8).
-__device__ __forceinline__ void advance_one(double mu_o, double var_o, float t_new, int32_t m, double& mu_n,
-                                            double& var_n) {
-    const double mm1 = double(m - 1), inv_m = 1.0 / double(m);
+// New (mu, var) of window i at length m from its values at m-1 (Eq. 7-8);
+// inv_m = 1/m.
+__device__ __forceinline__ void advance_one(double mu_o, double var_o, float t_new, int32_t m, double inv_m,
+                                            double& mu_n, double& var_n) {
+    const double mm1 = double(m - 1);
     const double d = mu_o - double(t_new);
     mu_n = (mm1 * mu_o + double(t_new)) * inv_m;
     var_n = mm1 * inv_m * (var_o + d * d * inv_m);
@@ -88,20 +89,24 @@ __global__ void k_stats(const Pass p, const int32_t* __restrict__ chain_first) {
         if (L.stats_mode != 0) {
             bool any_flat = false;
             float amax = 0.f, bmax = 0.f;
+            const double inv_m = 1.0 / double(m);
             for (int64_t i = tid; i < N; i += stride) {
                 double mu_i, var_i;
                 const float t_add = T[i + m - 1];
-                if (L.stats_mode == 1) advance_one(L.mu_src[i], L.var_src[i], t_add, m, mu_i, var_i);
+                if (L.stats_mode == 1) advance_one(L.mu_src[i], L.var_src[i], t_add, m, inv_m, mu_i, var_i);
                 else { mu_i = L.mu_src[i]; var_i = L.var_src[i]; }
                 L.mu[i] = mu_i;
                 L.var[i] = var_i;
-                const bool flat = sqrt(var_i) <= kFlatRel * fabs(mu_i);
+                // sigma <= 2^-22 |mu|, compared squared (a variance the recurrence
+                // left slightly negative counts as flat)
+                const double fl = kFlatRel * mu_i;
+                const bool flat = var_i <= fl * fl;
                 any_flat |= flat;
                 float df = 0.f, dg = 0.f;
                 if (i >= 1) {
                     // mu_{i-1} = mu_i - (t[i+m-1] - t[i-1]) / m for windows of one length
                     const double diff = double(t_add) - double(T[i - 1]);
-                    const double mu_p = mu_i - diff / double(m);
+                    const double mu_p = mu_i - diff * inv_m;
                     df = float(0.5 * diff);
                     dg = float((double(t_add) - mu_i) + (double(T[i - 1]) - mu_p));
                 }
