@@ -89,7 +89,7 @@ typedef struct {
                                 default 1e-3, must lie in [1e-6, 0.1] */
     int32_t select_cap;      /* max columns a select strip scans past its first
                                 (0 = default); pairs left unscanned go to refine */
-    int32_t use_graph;       /* 1: capture the batched form's launches in a CUDA graph */
+    int32_t reserved_a;      /* reserved, must be 0 */
     int32_t profile;         /* 1: time every kernel launch with CUDA events
                                 (palmad_get_stats) */
     int32_t pool_slots;      /* cap on the survivors refined at once (0 = as many as

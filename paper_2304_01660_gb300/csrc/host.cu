@@ -30,7 +30,7 @@ using namespace palmad;
 
 namespace {
 
-constexpr int kDefaultCap = 512;     // select columns past the strip triangle
+constexpr int kDefaultCap = 1024;    // select columns past the strip triangle
 constexpr int kRefineSeg = 512;      // refine sweep columns per work item (multiple of 256)
 constexpr int kMaxLanes = 4096;      // lanes per pass
 constexpr int64_t kPoolBytes = int64_t(1) << 30;  // per-chunk maxima of the refine pool
@@ -87,6 +87,12 @@ struct palmad_ctx {
     DBuf<double> pnn;
     Lane* h_lanes = nullptr;
     LaneState* h_st = nullptr;
+    // finalize's own pinned mirrors: its uploads may still be in flight when
+    // the next pass fills h_lanes / h_st (a pass synchronises before the
+    // next finalize refills these)
+    Lane* h_fin_lanes = nullptr;
+    LaneState* h_fin_st = nullptr;
+    int h_fin_cap = 0;
     int32_t* h_chain = nullptr;
     Small* h_small = nullptr;
     int64_t* h_pidx = nullptr;
@@ -527,17 +533,27 @@ palmad_status run_finalize(palmad_ctx* ctx, std::vector<PassLane>& req, const pa
     for (auto& q : req) need |= (q.lane.heat != nullptr) || (q.lane.count_out != nullptr);
     if (!need) return PALMAD_OK;
     CKS(ensure_pass(ctx, nl, 1));
+    if (ctx->h_fin_cap < nl) {
+        if (ctx->h_fin_lanes) cudaFreeHost(ctx->h_fin_lanes);
+        if (ctx->h_fin_st) cudaFreeHost(ctx->h_fin_st);
+        ctx->h_fin_lanes = nullptr;
+        ctx->h_fin_st = nullptr;
+        ctx->h_fin_cap = 0;
+        const int cap = std::max(nl, 64);
+        if (cudaMallocHost(&ctx->h_fin_lanes, sizeof(Lane) * cap) != cudaSuccess ||
+            cudaMallocHost(&ctx->h_fin_st, sizeof(LaneState) * cap) != cudaSuccess)
+            return fail(ctx, PALMAD_ERR_OOM, "pinned host allocation failed");
+        ctx->h_fin_cap = cap;
+    }
     for (int l = 0; l < nl; ++l) {
-        ctx->h_lanes[l] = req[l].lane;
-        ctx->h_st[l] = req[l].state;
-        ctx->h_st[l].count_final = 0;
+        ctx->h_fin_lanes[l] = req[l].lane;
+        ctx->h_fin_st[l] = req[l].state;
+        ctx->h_fin_st[l].count_final = 0;
     }
     Pass p = base_pass(ctx, nl, 1, true, o);
-    CK(cudaMemcpyAsync(ctx->lanes.p, ctx->h_lanes, sizeof(Lane) * nl, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->st.p, ctx->h_st, sizeof(LaneState) * nl, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->lanes.p, ctx->h_fin_lanes, sizeof(Lane) * nl, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->st.p, ctx->h_fin_st, sizeof(LaneState) * nl, cudaMemcpyHostToDevice, ctx->stream));
     LAUNCH(PALMAD_K_HEAT, launch_finalize(p, ctx->stream));
-    // the pinned mirrors are reused by the next pass: make sure the copies are done
-    CK(cudaStreamSynchronize(ctx->stream));
     return PALMAD_OK;
 }
 
@@ -961,7 +977,7 @@ palmad_status palmad_default_options(palmad_options* opt) {
     opt->batch_lengths = 0;
     opt->band_rel = 1e-3;
     opt->select_cap = 0;
-    opt->use_graph = 0;
+    opt->reserved_a = 0;
     opt->profile = 0;
     return PALMAD_OK;
 }
@@ -1012,6 +1028,8 @@ void palmad_destroy(palmad_ctx* ctx) {
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     if (ctx->h_chain) cudaFreeHost(ctx->h_chain);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
+    if (ctx->h_fin_lanes) cudaFreeHost(ctx->h_fin_lanes);
+    if (ctx->h_fin_st) cudaFreeHost(ctx->h_fin_st);
     if (ctx->h_pidx) cudaFreeHost(ctx->h_pidx);
     if (ctx->h_pnn) cudaFreeHost(ctx->h_pnn);
     for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);

@@ -183,7 +183,7 @@ __device__ __forceinline__ void first_col_seeds(const LaneView& a, int64_t r0, i
 }
 
 template <int D, bool REFINE>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, REFINE ? 4 : 3) k_sweep(const Pass p) {
+__global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(const Pass p) {
     constexpr int H = 32 * D;
     extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -20,7 +20,7 @@ namespace palmad {
 
 constexpr int kWarp = 32;
 constexpr float kInf = __builtin_huge_valf();
-constexpr int kStripH = 256;   // rows per strip of the select sweep (32 lanes x 8)
+constexpr int kStripH = 128;   // rows per strip of the select sweep (32 lanes x 4)
 constexpr int kRefineH = 128;  // rows per strip of the refine sweep (32 lanes x 4)
 constexpr int kCoarse = 512;   // columns per coarse block of the chunk maxima (= refine segment)
 constexpr int kSelPieceCols = 512;  // columns per select work item (a strip's scan is cut into pieces)

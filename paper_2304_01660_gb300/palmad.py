@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
         ("batch_lengths", ctypes.c_int32),
         ("band_rel", ctypes.c_double),
         ("select_cap", ctypes.c_int32),
-        ("use_graph", ctypes.c_int32),
+        ("reserved_a", ctypes.c_int32),
         ("profile", ctypes.c_int32),
         ("pool_slots", ctypes.c_int32),
         ("direct_below", ctypes.c_int32),
