@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
         const double ic = flatc ? 0.0 : 1.0 / sqrt(varc);
         const bool zc_smem = m <= kRecheckWin;
         if (zc_smem)
-            for (int k = lane; k < m; k += 32) zc[k] = (double(T[c + k]) - muc) * ic;
+            for (int k = lane; k < m; k += 32) zc[k] = __dmul_rn(double(T[c + k]) - muc, ic);
         __syncwarp();
         const float* arow = p.acen + g * int64_t(p.kpad_max);
         const float* cm = p.cmax + g * int64_t(p.nchunks_max);
@@ -405,9 +405,12 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
                         else if (flatc || flatj) d2 = 2.0 * m;
                         else {
                             const double ij = 1.0 / sqrt(varj);
+                            // each z value rounded on its own (no FMA contraction), so
+                            // d(c, j) and d(j, c) are bit-identical and ties break by index
                             for (int k = lane; k < m; k += 32) {
-                                const double zck = zc_smem ? zc[k] : (double(T[c + k]) - muc) * ic;
-                                const double x = zck - (double(T[jc + k]) - muj) * ij;
+                                const double zck = zc_smem ? zc[k] : __dmul_rn(double(T[c + k]) - muc, ic);
+                                const double zjk = __dmul_rn(double(T[jc + k]) - muj, ij);
+                                const double x = zck - zjk;
                                 d2 = fma(x, x, d2);
                             }
 #pragma unroll
