@@ -175,8 +175,8 @@ def run_ours(args, w):
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    if rank == 0 or not os.path.exists(palmad.LIB_PATH):
-        _build.build()
+    if rank == 0:
+        _build.build()  # one rank compiles; the others wait for it
     if world > 1:
         dist.barrier()
 
