@@ -31,7 +31,7 @@ using namespace palmad;
 namespace {
 
 constexpr int kDefaultCap = 1024;    // select columns past the strip triangle
-constexpr int kRefineSeg = 512;      // refine sweep columns per work item (multiple of 256)
+constexpr int kRefineSeg = 1024;      // refine sweep columns per work item (multiple of 256)
 constexpr int kMaxLanes = 4096;      // lanes per pass
 constexpr int64_t kPoolBytes = int64_t(1) << 30;  // per-chunk maxima of the refine pool
 constexpr int64_t kSeedBytes = int64_t(1) << 30;  // tensor-core top-row seeds of the refine sweep

@@ -376,11 +376,12 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
             while (bq2) {
                 const int32_t q2 = cb + __ffs(bq2) - 1;
                 bq2 &= bq2 - 1;
-                // chunks of the coarse block (16 of them) above the threshold
-                const int32_t q = q2 * (kCoarse / 32) + lane;
-                uint32_t bq = __ballot_sync(kFull, lane < kCoarse / 32 && q < nchunks && cm[q] >= thr);
+                // chunks of the coarse block above the threshold, 32 at a time
+                for (int32_t qb = q2 * (kCoarse / 32); qb < (q2 + 1) * (kCoarse / 32); qb += 32) {
+                const int32_t q = qb + lane;
+                uint32_t bq = __ballot_sync(kFull, q < (q2 + 1) * (kCoarse / 32) && q < nchunks && cm[q] >= thr);
                 while (bq) {
-                    const int32_t qq = q2 * (kCoarse / 32) + __ffs(bq) - 1;
+                    const int32_t qq = qb + __ffs(bq) - 1;
                     bq &= bq - 1;
                     // FP32 rho of the chunk's columns, one per lane
                     const int64_t j = int64_t(qq) * 32 + lane;
@@ -422,6 +423,7 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
                             ++fp64;
                         }
                     }
+                }
                 }
             }
         }

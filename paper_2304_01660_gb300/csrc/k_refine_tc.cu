@@ -74,6 +74,9 @@ __host__ __device__ inline TcLayout tc_layout(int kp, int ns) {
     return t;
 }
 
+static_assert((kTcM * kTcTiles) % kCoarse == 0 && (kTcM * kTcTiles) / kCoarse <= 2,
+              "a work item covers one or two whole coarse blocks");
+
 template <int NS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
     extern __shared__ __align__(1024) unsigned char smem[];

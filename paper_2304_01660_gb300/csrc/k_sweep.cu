@@ -18,7 +18,7 @@
 //     candidate bit (Cand and Neighbor of Algorithm 3 are one bitmap here,
 //     since refine ANDs them anyway); the warp leaves the strip once every
 //     row is dead (Algorithm 3 lines 14-15) or after `cap` columns;
-//   * refine sweeps a 2048-column segment of every strip that holds enough
+//   * refine sweeps a 1024-column segment of every strip that holds enough
 //     survivors (both sides of the exclusion zone |i - j| < m, which is
 //     masked), starting from directly computed first-column dot products;
 //     per survivor it records the maximum rho of every 32-column chunk, and
