@@ -31,7 +31,9 @@ using namespace palmad;
 namespace {
 
 constexpr int kDefaultCap = 1024;    // select columns past the strip triangle
-constexpr int kRefineSeg = 1024;      // refine sweep columns per work item (multiple of 256)
+constexpr int kRefineSeg = 1024;      // refine sweep columns per work item (multiple of 256) ...
+constexpr int kRefineSegLong = 2048;  // ... and for passes with many columns (lanes x N >= kLongPass)
+constexpr int64_t kLongPass = 2000000;
 constexpr int kMaxLanes = 4096;      // lanes per pass
 constexpr int64_t kPoolBytes = int64_t(1) << 30;  // per-chunk maxima of the refine pool
 constexpr int64_t kSeedBytes = int64_t(1) << 30;  // tensor-core top-row seeds of the refine sweep
@@ -320,7 +322,7 @@ palmad_status ensure_pool(palmad_ctx* ctx, int32_t kpad, int32_t nchunks) {
     if (ctx->pool > 0 && kpad <= ctx->pool_kpad && nchunks <= ctx->pool_nchunks) return PALMAD_OK;
     kpad = std::max(kpad, ctx->pool_kpad);
     nchunks = std::max(nchunks, ctx->pool_nchunks);
-    const int64_t ncoarse = (int64_t(nchunks) * 32 + kCoarse - 1) / kCoarse;
+    const int64_t ncoarse = (int64_t(nchunks) * 32 + kCoarseMin - 1) / kCoarseMin;
     int64_t slots = kPoolBytes / (int64_t(sizeof(float)) * (nchunks + ncoarse + kpad));
     slots = std::min<int64_t>(slots, 1 << 17);
     slots = std::max<int64_t>(64, (slots / 64) * 64);
@@ -346,7 +348,7 @@ Pass base_pass(palmad_ctx* ctx, int nl, int K, bool exclusive, const palmad_opti
     p.K = K;
     p.exclusive = exclusive ? 1 : 0;
     p.seg = kRefineSeg;
-    static_assert(kRefineSeg == kCoarse, "a refine segment is one coarse block of the chunk maxima");
+    static_assert(kRefineSeg >= kCoarseMin && kRefineSegLong % kRefineSeg == 0, "segments cover the coarse pool");
     p.cap = o.select_cap > 0 ? o.select_cap : kDefaultCap;
     p.slot_lane = ctx->slot_lane.p;
     p.slot_win = ctx->slot_win.p;
@@ -409,7 +411,14 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     p.kpad_max = ctx->pool_kpad;
     p.kpad_pass = kpad_max;
     p.nchunks_max = ctx->pool_nchunks;
-    p.ncoarse_max = int32_t((int64_t(ctx->pool_nchunks) * 32 + kCoarse - 1) / kCoarse);
+    p.ncoarse_max = int32_t((int64_t(ctx->pool_nchunks) * 32 + kCoarseMin - 1) / kCoarseMin);
+    {
+        // long passes: 2048-column segments (fewer items, each first-column
+        // seed spread over more columns); short ones keep 1024 for balance
+        int64_t cols = 0;
+        for (int l = 0; l < nl; ++l) cols += ctx->h_lanes[l].N;
+        p.seg = cols >= kLongPass ? kRefineSegLong : kRefineSeg;
+    }
     p.mixed = (o.precision == PALMAD_PREC_MIXED && refine_tc_supported(p)) ? 1 : 0;
     p.direct_below = o.direct_below;
     p.strip_row = ctx->strip_row.p;

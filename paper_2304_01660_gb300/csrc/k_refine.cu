@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
             if (lane == 0 && sok) {
                 if (mx > -kInf) {
                     atomicMax(&p.gmax[g], enc_f32(mx));
-                    atomicMax(&p.cmax2[g * p.ncoarse_max + (j0 / kCoarse)], enc_f32(mx));  // tile inside one block
+                    atomicMax(&p.cmax2[g * p.ncoarse_max + (j0 / p.seg)], enc_f32(mx));  // tile inside one block
                 }
                 if (mx > rho_prune) p.dead[g] = 1;
             }
@@ -369,7 +369,8 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
         const float* cm = p.cmax + g * int64_t(p.nchunks_max);
         const uint32_t* c2 = p.cmax2 + g * int64_t(p.ncoarse_max);
         const int32_t nchunks = int32_t((N + 31) / 32);
-        const int32_t ncoarse = int32_t((N + kCoarse - 1) / kCoarse);
+        const int32_t ncoarse = int32_t((N + p.seg - 1) / p.seg);
+        const int32_t cpb = p.seg / 32;  // chunks per coarse block
         for (int32_t cb = 0; cb < ncoarse; cb += 32) {
             const int32_t q2l = cb + lane;
             uint32_t bq2 = __ballot_sync(kFull, q2l < ncoarse && c2[q2l] >= thr_enc);
@@ -377,9 +378,9 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
                 const int32_t q2 = cb + __ffs(bq2) - 1;
                 bq2 &= bq2 - 1;
                 // chunks of the coarse block above the threshold, 32 at a time
-                for (int32_t qb = q2 * (kCoarse / 32); qb < (q2 + 1) * (kCoarse / 32); qb += 32) {
+                for (int32_t qb = q2 * cpb; qb < (q2 + 1) * cpb; qb += 32) {
                 const int32_t q = qb + lane;
-                uint32_t bq = __ballot_sync(kFull, q < (q2 + 1) * (kCoarse / 32) && q < nchunks && cm[q] >= thr);
+                uint32_t bq = __ballot_sync(kFull, q < (q2 + 1) * cpb && q < nchunks && cm[q] >= thr);
                 while (bq) {
                     const int32_t qq = qb + __ffs(bq) - 1;
                     bq &= bq - 1;

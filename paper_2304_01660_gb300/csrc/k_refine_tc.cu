@@ -74,8 +74,9 @@ __host__ __device__ inline TcLayout tc_layout(int kp, int ns) {
     return t;
 }
 
-static_assert((kTcM * kTcTiles) % kCoarse == 0 && (kTcM * kTcTiles) / kCoarse <= 2,
-              "a work item covers one or two whole coarse blocks");
+// a tile lies inside one coarse block (p.seg is a multiple of 1024), and a
+// work item of kTcM * kTcTiles = 1024 columns touches one block
+static_assert(kCoarseMin % kTcM == 0 && kTcM * kTcTiles <= kCoarseMin, "tiles and items inside coarse blocks");
 
 template <int NS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
                     const int32_t g = s_slot[s];
                     const float lo = keep - epsmax;
                     p.cmax[int64_t(g) * p.nchunks_max + chunk] = keep + epsmax;
-                    atomicMax(&s_c2[(t * kTcM) / kCoarse * NS + s], enc_f32(keep + epsmax));
+                    atomicMax(&s_c2[s], enc_f32(keep + epsmax));
                     if (lo > -kInf) atomicMax(&s_lo[s], enc_f32(lo));
                     if (lo > rp) p.dead[g] = 1;
                 }
@@ -321,10 +322,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
         }
         if (tid < nd) {
             if (s_lo[tid]) atomicMax(&p.gmax[s_slot[tid]], s_lo[tid]);
-            // the item's columns are whole coarse blocks (jstart is a multiple of 1024)
-            for (int b2 = 0; b2 < (kTcM * kTcTiles) / kCoarse; ++b2)
-                if (jstart + int64_t(b2) * kCoarse < N)
-                    p.cmax2[int64_t(s_slot[tid]) * p.ncoarse_max + jstart / kCoarse + b2] = s_c2[b2 * NS + tid];
+            // the coarse block holding the item (rows zeroed by the plan;
+            // with 2048-column blocks two items share one)
+            atomicMax(&p.cmax2[int64_t(s_slot[tid]) * p.ncoarse_max + jstart / p.seg], s_c2[tid]);
         }
         __syncthreads();
     }

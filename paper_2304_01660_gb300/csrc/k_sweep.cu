@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
         __syncwarp();
         if (REFINE) {
             // the segment is one coarse block: its maximum is this row's tmax
-            const int64_t qb = ja / kCoarse;
+            const int64_t qb = ja / p.seg;
 #pragma unroll
             for (int d = 0; d < D; ++d)
                 if (slot[d] >= 0) {

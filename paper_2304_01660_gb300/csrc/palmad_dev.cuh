@@ -22,7 +22,7 @@ constexpr int kWarp = 32;
 constexpr float kInf = __builtin_huge_valf();
 constexpr int kStripH = 128;   // rows per strip of the select sweep (32 lanes x 4)
 constexpr int kRefineH = 128;  // rows per strip of the refine sweep (32 lanes x 4)
-constexpr int kCoarse = 1024;   // columns per coarse block of the chunk maxima (= refine segment)
+constexpr int kCoarseMin = 1024;  // smallest coarse block of the chunk maxima (the pool is sized for it)
 constexpr int kSelPieceCols = 512;  // columns per select work item (a strip's scan is cut into pieces)
 constexpr int kMaxK = 1024;    // largest top-K
 
@@ -131,7 +131,8 @@ struct Pass {
     int32_t* dead;         // [slots]
     unsigned long long* nn2;  // [slots] FP64 bits of the smallest d^2
     float* cmax;           // [slots][nchunks_max] maximum rho per 32-column chunk
-    uint32_t* cmax2;       // [slots][ncoarse_max] enc_f32 of the maximum per coarse block (kCoarse columns)
+    uint32_t* cmax2;       // [slots][ncoarse_max] enc_f32 of the maximum per coarse block (seg columns:
+                           //   a refine segment is one coarse block; 1024 or 2048)
     int32_t ncoarse_max;
     int32_t pad6;
     int2* strips;          // (lane, strip) swept by refine
