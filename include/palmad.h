@@ -103,7 +103,8 @@ typedef struct {
                                 keeps every seed on the CUDA cores, which measured faster */
     int32_t seed_rows_max;   /* cap on tensor-core seed rows per refine round (0 = as many
                                 as 1 GiB holds); strips past the cap seed on the CUDA cores */
-    int32_t reserved[1];
+    int32_t refine_seg;      /* columns per refine sweep work item: 0 = automatic (2048 for
+                                passes holding >= 2e6 columns, else 1024), or 1024 / 2048 */
 } palmad_options;
 
 /* Per-call counters of the most recent find/drag call. */

@@ -261,6 +261,8 @@ palmad_status read_options(palmad_ctx* ctx, const palmad_options* in, palmad_opt
     if (o.direct_below < 0) return fail(ctx, PALMAD_ERR_ARG, "direct_below must be >= 0");
     if (o.tc_seed_min < 0) return fail(ctx, PALMAD_ERR_ARG, "tc_seed_min must be >= 0");
     if (o.seed_rows_max < 0) return fail(ctx, PALMAD_ERR_ARG, "seed_rows_max must be >= 0");
+    if (o.refine_seg != 0 && o.refine_seg != kRefineSeg && o.refine_seg != kRefineSegLong)
+        return fail(ctx, PALMAD_ERR_ARG, "refine_seg must be 0, 1024 or 2048");
     return PALMAD_OK;
 }
 
@@ -417,7 +419,7 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
         // seed spread over more columns); short ones keep 1024 for balance
         int64_t cols = 0;
         for (int l = 0; l < nl; ++l) cols += ctx->h_lanes[l].N;
-        p.seg = cols >= kLongPass ? kRefineSegLong : kRefineSeg;
+        p.seg = o.refine_seg ? o.refine_seg : (cols >= kLongPass ? kRefineSegLong : kRefineSeg);
     }
     p.mixed = (o.precision == PALMAD_PREC_MIXED && refine_tc_supported(p)) ? 1 : 0;
     p.direct_below = o.direct_below;

@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
         ("direct_below", ctypes.c_int32),
         ("tc_seed_min", ctypes.c_int32),
         ("seed_rows_max", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 1),
+        ("refine_seg", ctypes.c_int32),
     ]
 
 

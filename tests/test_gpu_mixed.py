@@ -154,3 +154,16 @@ def test_tc_seeds_equal_fp32_full_size(ctx):
         for k in ("idx", "nn", "count", "r", "heatmap"):
             np.testing.assert_array_equal(a[k], b[k])
         assert ctx.palmad_get_stats()["seed_pairs"] > 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["rw3000", "sine4000", "flat2200"])
+def test_long_refine_segments(ctx, prec, name):
+    """2048-column refine segments (automatic on long passes), forced here."""
+    T = SERIES[name]()
+    for m in (8, 100):
+        mp, _ = oracle.matrix_profile(T, m)
+        for r in _thresholds(mp, (0.5, 0.99)):
+            _check_drag(ctx, T, m, float(r), _opts(precision=prec, refine_seg=2048))
+    got = ctx.palmad_find_discords(T, 16, 40, 2, _opts(precision=prec, refine_seg=2048, batch_lengths=8), heatmap=True)
+    _check_merlin(got, oracle.merlin(T, 16, 40, 2, True, heatmap=True), heat=True)
