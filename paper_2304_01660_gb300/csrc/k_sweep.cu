@@ -9,9 +9,10 @@
 //     (cov(i,j) = cov(i-1,j-1) + df_i dg_j + df_j dg_i); the value of the row
 //     above arrives from the previous lane by one shuffle;
 //   * the strip's top row has no row above: its dot products ("QTrow" of
-//     Algorithm 3) are computed per chunk by a transposed register-blocked
-//     pass over the staged series, then reduce-scattered so that lane l
-//     holds column c0 + l;
+//     Algorithm 3) are computed per chunk by a register-blocked pass over
+//     the staged series (4 groups of 8 columns, each lane one eighth of the
+//     window in interleaved blocks of 4), then reduce-scattered within each
+//     group;
 //   * select scans to the right (j >= i + m) from the strip's triangle, as
 //     the paper's segment-scans-right; a pair with rho > rho_prune (d < r
 //     beyond the FP32 error band) clears the row's and the column's
@@ -94,54 +95,61 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Sum over lanes of acc[c] lands in lane c (reduce-scatter, 31 shuffles).
-__device__ __forceinline__ float reduce_scatter32(float (&acc)[32], int lane) {
+// Reduce-scatter over the 8 lanes of a column group (lanes g, g+4, ..., g+28):
+// the group's sum of acc[c] lands in the lane whose k-slice index
+// ks = lane >> 2 equals c (3 shuffle stages).
+__device__ __forceinline__ float reduce_scatter8(float (&acc)[8], int lane) {
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
+    for (int o = 16, w = 4; o >= 4; o >>= 1, w >>= 1) {
         const bool upper = (lane & o) != 0;
 #pragma unroll
-        for (int k = 0; k < o; ++k) {
-            const float send = upper ? acc[k] : acc[k + o];
-            const float keep = upper ? acc[k + o] : acc[k];
+        for (int k = 0; k < w; ++k) {
+            const float send = upper ? acc[k] : acc[k + w];
+            const float keep = upper ? acc[k + w] : acc[k];
             acc[k] = keep + __shfl_xor_sync(kFull, send, o);
         }
     }
     return acc[0];
 }
 
-// Top-row dot products cov(top, c0 + lane) of one chunk from the staged
-// buffer b (series slice minus the offset b0 = mu of column c0).
+// Top-row dot products cov(top, c0 + c) of one chunk's 32 columns from the
+// staged buffer b (series slice minus the offset b0 = mu of column c0).
+// Lane = ks*4 + g: column group g (columns 8g .. 8g+7) and k-slice ks, the
+// blocks k = 32t + 4ks .. 32t + 4ks + 3 (t = 0 .. kp/32 - 1).  Interleaving
+// the slices in blocks of 4 puts the 8 lanes of every quarter-warp on 8
+// distinct 16-byte bank groups for both the series and the window loads, so
+// the 128-bit shared loads run without bank conflicts.  Each lane
+// accumulates its 8 columns over its slice, then the group's 8 lanes
+// reduce-scatter so that lane (g, ks) holds column 8g + ks.
 __device__ __forceinline__ void chunk_seeds(const LaneView& a, const WarpSmem& sm, int kps, int b, int64_t c0,
                                             float suma, int kp, int lane) {
-    const int s4 = kp / 32;
     float* tw = sm.tw + b * (kps + 32);
     const float4* cr = sm.colrec + b * 32;
     const float b0 = cr[0].w;
     for (int x = lane; x < kp + 32; x += 32) tw[x] -= b0;
     __syncwarp();
-    float acc[32];
+    const int g = lane & 3, ks = lane >> 2;
+    float acc[8];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0.f;
-    const int kl = lane * s4;
-    for (int q = 0; q < s4; q += 4) {
-        const float4 av = *reinterpret_cast<const float4*>(sm.ahat + kl + q);
+    for (int c = 0; c < 8; ++c) acc[c] = 0.f;
+    const float* ap = sm.ahat + 4 * ks;
+    const float* tp = tw + 8 * g + 4 * ks;
+    for (int q = 0; q < kp; q += 32) {
+        const float4 av = *reinterpret_cast<const float4*>(ap + q);
+        const float4 t0 = *reinterpret_cast<const float4*>(tp + q);
+        const float4 t1 = *reinterpret_cast<const float4*>(tp + q + 4);
+        const float4 t2 = *reinterpret_cast<const float4*>(tp + q + 8);
         const float a4[4] = {av.x, av.y, av.z, av.w};
+        const float tv[12] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x, t2.y, t2.z, t2.w};
 #pragma unroll
-        for (int cb = 0; cb < 4; ++cb) {
-            const float* tp = tw + kl + q + cb * 8;
-            const float4 t0 = *reinterpret_cast<const float4*>(tp);
-            const float4 t1 = *reinterpret_cast<const float4*>(tp + 4);
-            const float4 t2 = *reinterpret_cast<const float4*>(tp + 8);
-            const float tv[12] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x, t2.y, t2.z, t2.w};
+        for (int qq = 0; qq < 4; ++qq)
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq)
-#pragma unroll
-                for (int cc = 0; cc < 8; ++cc) acc[cb * 8 + cc] = fmaf(a4[qq], tv[qq + cc], acc[cb * 8 + cc]);
-        }
+            for (int c = 0; c < 8; ++c) acc[c] = fmaf(a4[qq], tv[qq + c], acc[c]);
     }
-    const float dot = reduce_scatter32(acc, lane);
-    const int64_t j = c0 + lane;
-    sm.seed[lane] = (j < a.N) ? dot - (cr[lane].w - b0) * suma : 0.f;
+    const float dot = reduce_scatter8(acc, lane);
+    const int col = g * 8 + ks;
+    const int64_t j = c0 + col;
+    sm.seed[col] = (j < a.N) ? dot - (cr[col].w - b0) * suma : 0.f;
     __syncwarp();
 }
 
