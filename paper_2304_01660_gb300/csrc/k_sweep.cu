@@ -89,6 +89,13 @@ __device__ __forceinline__ void issue_chunk(const LaneView& a, const WarpSmem& s
     cp_async_commit();
 }
 
+// max(a, b, c) in one instruction (three-input max.f32, sm_100 and later).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -350,11 +357,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
             if (REFINE) masked = !(c0 >= i0 + H - 1 + m || c0 + 31 <= i0 - m);
             else masked = (c0 - jt) < int64_t(H - 1);
             uint32_t colmask = 0;
-            // One column step: every row advances along its diagonal (Eq. 9),
-            // then rho (up to the row factor) feeds the row maxima and, in
-            // select, the column mark.
-            auto step = [&](int st, bool first_col, bool mask) {
-                const int64_t j = c0 + st;
+            // One column: every row advances along its diagonal (Eq. 9), and
+            // x[d] = cov * inv_j is rho up to the row factor.
+            auto advance = [&](int st, bool first_col, float (&x)[D]) {
                 const float4 cr = crb[st];
                 const float sd = seedv[st];
                 const float up = __shfl_up_sync(kFull, cov[D - 1], 1);
@@ -363,26 +368,48 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
                     for (int d = D - 1; d >= 1; --d) cov[d] = fmaf(df_r[d], cr.y, fmaf(cr.x, dg_r[d], cov[d - 1]));
                     cov[0] = (lane == 0) ? sd : fmaf(df_r[0], cr.y, fmaf(cr.x, dg_r[0], up));
                 }
+#pragma unroll
+                for (int d = 0; d < D; ++d) x[d] = cov[d] * cr.z;
+            };
+            // One column step: x feeds the row maxima and, in select, the
+            // column mark (pairs inside the exclusion zone masked out).
+            auto step = [&](int st, bool first_col, bool mask) {
+                float x[D];
+                advance(st, first_col, x);
                 bool pred = false;
-                const int64_t lim = j - r0;  // j - i for d = 0
+                const int64_t lim = c0 + st - r0;  // j - i for d = 0
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
-                    float x = cov[d] * cr.z;
                     if (mask) {
                         const int64_t dj = lim - d;  // j - i
                         const bool ok = REFINE ? (dj >= m || dj <= -int64_t(m)) : (dj >= m);
-                        x = ok ? x : -kInf;
+                        x[d] = ok ? x[d] : -kInf;
                     }
-                    rmax[d] = fmaxf(rmax[d], x);
-                    if (!REFINE) pred |= x > thr_r[d];
+                    rmax[d] = fmaxf(rmax[d], x[d]);
+                    if (!REFINE) pred |= x[d] > thr_r[d];
                 }
                 if (!REFINE && pred) colmask |= 1u << st;
             };
             if (!masked && st0 == 0 && steps == 32 && !(seeded && c0 == ja)) {
-                // full unmasked chunk: unrolled so loads and FMAs of
-                // consecutive steps interleave
+                // full unmasked chunk, unrolled so loads and FMAs of
+                // consecutive steps interleave; two columns per iteration
+                // enter the row maxima through one three-input max
 #pragma unroll
-                for (int st = 0; st < 32; ++st) step(st, false, false);
+                for (int st = 0; st < 32; st += 2) {
+                    float x0[D], x1[D];
+                    advance(st, false, x0);
+                    advance(st + 1, false, x1);
+                    bool p0 = false, p1 = false;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        rmax[d] = fmax3(rmax[d], x0[d], x1[d]);
+                        if (!REFINE) {
+                            p0 |= x0[d] > thr_r[d];
+                            p1 |= x1[d] > thr_r[d];
+                        }
+                    }
+                    if (!REFINE) colmask |= (p0 ? 1u << st : 0u) | (p1 ? 2u << st : 0u);
+                }
             } else {
                 for (int st = st0; st < steps; ++st) step(st, seeded && c0 + st == ja, masked);
             }
