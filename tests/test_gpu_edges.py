@@ -71,3 +71,20 @@ def test_large_topk_against_brute_force(ctx, form, excl):
             np.testing.assert_array_equal(got["idx"][l], wi)
             np.testing.assert_allclose(got["nn"][l], wn, rtol=1e-5, atol=0)
         assert (got["idx"][l] >= 0).sum() == (wi >= 0).sum() or got["r"][l] > 0
+
+
+@pytest.mark.parametrize("form", FORMS + [dict(precision=1)])
+@pytest.mark.parametrize("m", [900, 1000])
+def test_widest_windows_drag(ctx, form, m):
+    """Windows padded to 1024, the widest the tensor-core refine takes: the
+    sweep's top-row seed pass runs its longest k range."""
+    from test_gpu_parity import _check_drag, _thresholds
+    for T in (synth.random_walk(3200, 71), synth.workload("sine100k").series[0][:3400]):
+        mp, _ = oracle.matrix_profile(T, m)
+        for r in _thresholds(mp, (0.2, 0.9, 1.0)):
+            _check_drag(ctx, T, m, float(r), _opts(**form))
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_widest_windows_merlin(ctx, form):
+    _merlin(ctx, synth.random_walk(3200, 71), 994, 1000, 2, form)
