@@ -63,7 +63,7 @@ typedef enum {
     PALMAD_ERR_OOM = -3,         /* device or pinned host allocation failed */
     PALMAD_ERR_CUDA = -4,        /* a CUDA runtime call or kernel failed */
     PALMAD_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
-    PALMAD_ERR_UNSUPPORTED = -6, /* option or size not supported by this build */
+    PALMAD_ERR_UNSUPPORTED = -6, /* option or size not supported by the library */
     PALMAD_ERR_INTERNAL = -7,    /* an internal consistency check failed */
     PALMAD_ERR_TOO_LARGE = -8    /* size beyond the fixed scratch of palmad_topk_profile_noalloc */
 } palmad_status;
