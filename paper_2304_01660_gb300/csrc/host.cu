@@ -408,7 +408,15 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     ctx->sets_dirty = true;
     Pass p = base_pass(ctx, nl, K, exclusive, o);
     p.sel_items = strips;
-    p.sel_pieces = int32_t((kStripH + 31 + p.cap + kSelPieceCols - 1) / kSelPieceCols);
+    {
+        // a pass with few strips (one lane, a rerun) would leave most warps
+        // idle while each runs a long piece: shorter pieces spread its scan
+        const int64_t slots = int64_t(ctx->sms) * 4 * 4;  // resident select warps
+        const int64_t cols = kStripH + 31 + p.cap;
+        p.sel_cols = (strips * ((cols + kSelPieceCols - 1) / kSelPieceCols) < 2 * slots) ? kSelPieceColsShort
+                                                                                           : kSelPieceCols;
+        p.sel_pieces = int32_t((cols + p.sel_cols - 1) / p.sel_cols);
+    }
     p.nmax = nmax;
     p.kpad_max = ctx->pool_kpad;
     p.kpad_pass = kpad_max;

@@ -261,9 +261,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
         } else {
             jt = s * H + m;
             if (jt >= N) continue;  // no window to the right: column marks / refine decide these rows
-            const int64_t pc = (jt & ~int64_t(31)) + piece * int64_t(kSelPieceCols);
+            const int64_t pc = (jt & ~int64_t(31)) + piece * int64_t(p.sel_cols);
             ja = piece == 0 ? jt : pc;
-            jb = min64(min64(N, s * H + H - 1 + m + p.cap), pc + kSelPieceCols);
+            jb = min64(min64(N, s * H + H - 1 + m + p.cap), pc + p.sel_cols);
             if (ja >= jb) continue;
         }
         // rows start from directly computed dot products at column ja

@@ -23,7 +23,8 @@ constexpr float kInf = __builtin_huge_valf();
 constexpr int kStripH = 128;   // rows per strip of the select sweep (32 lanes x 4)
 constexpr int kRefineH = 128;  // rows per strip of the refine sweep (32 lanes x 4)
 constexpr int kCoarseMin = 1024;  // smallest coarse block of the chunk maxima (the pool is sized for it)
-constexpr int kSelPieceCols = 512;  // columns per select work item (a strip's scan is cut into pieces)
+constexpr int kSelPieceCols = 512;       // columns per select work item (a strip's scan is cut into pieces)
+constexpr int kSelPieceColsShort = 256;  // the same for passes with too few strips to fill the GPU
 constexpr int kMaxK = 1024;    // largest top-K
 
 // Per-window data the FP32 kernels read, one 16-byte record per window:
@@ -111,6 +112,7 @@ struct Pass {
     int64_t cap;           // select columns per strip past its triangle
     int64_t sel_items;     // total select strips
     int32_t sel_pieces;    // column pieces per select strip
+    int32_t sel_cols;      // columns per select piece (multiple of 32)
     int32_t direct_below;  // > 0: strips with fewer survivors take the direct form
     int64_t nmax;          // largest N over the lanes
     // refine pool (this round)
