@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per launch of a kernel from an ncu capture of the
 # current kernel source (profiles/); None once the kernel changes.
 TRAFFIC_PER_LAUNCH: dict[str, float | None] = {
-    "refine_sweep": 105.252352e6 + 131.402496e6,  # profiles/k_sweep_sine100k.md
+    "refine_sweep": 105.408512e6 + 130.19904e6,  # profiles/k_sweep_sine100k.md
 }
 
 
