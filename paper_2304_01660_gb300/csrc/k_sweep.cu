@@ -1,9 +1,9 @@
 // Strip sweeps: candidate select (DRAG phase 1; Algorithm 3, Sec. 3.2) and
 // the recurrence form of refine (DRAG phase 2; Algorithm 4, Sec. 3.3).
 //
-// A warp owns a strip of H = 32*D consecutive windows (rows i; D = 8 in
-// select, 4 in refine) and steps
-// across a range of windows (columns j), 32 columns per chunk:
+// A warp owns a strip of H = 32*D consecutive windows (rows i; D = 4, so
+// 128 rows, in both sweeps) and steps across a range of windows (columns j),
+// 32 columns per chunk:
 //   * lane l holds rows i0 + l*D .. i0 + l*D + D-1 in registers; one step
 //     advances every row by one column with the diagonal recurrence of Eq. 9
 //     (cov(i,j) = cov(i-1,j-1) + df_i dg_j + df_j dg_i); the value of the row
