@@ -59,6 +59,11 @@ def _load():
                                         _i64p, _f64p]
             lib.oracle_merlin.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int, _i64p, _f64p, _i64p, _f64p, _i32p, _f32p]
+            lib.oracle_knn.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _f64p]
+            lib.oracle_drag_knn.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                            _f64p, _i64p, _f64p, ctypes.c_int64, _i64p]
+            lib.oracle_merlin_knn.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int, ctypes.c_int32, _i64p, _f64p, _i64p, _f64p, _i32p, _f32p]
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -114,6 +119,35 @@ def nn_one(T, m: int, i: int):
     return nn.value, idx.value
 
 
+def knn_profile(T, m: int, k: int):
+    """k-distance of every window (reading R14): the k-th smallest distance
+    to its non-self matches, by brute force; inf where a window has fewer
+    than k non-self matches."""
+    T = _f32(T)
+    out = np.empty(len(T) - m + 1)
+    rc = _load().oracle_knn(_p(T, _f32p), len(T), m, k, _p(out, _f64p))
+    if rc:
+        raise ValueError(f"oracle_knn rc={rc}")
+    return out
+
+
+def drag_knn(T, m: int, k: int, r: float):
+    """Range k-discords of length m at threshold r (reading R14): ascending
+    indices and their k-distances."""
+    T = _f32(T)
+    cap = 1024
+    while True:
+        idx, nn = np.empty(cap, dtype=np.int64), np.empty(cap)
+        cnt = ctypes.c_int64(0)
+        rc = _load().oracle_drag_knn(_p(T, _f32p), len(T), m, k, float(r), None, _p(idx, _i64p), _p(nn, _f64p),
+                                     cap, ctypes.byref(cnt))
+        if rc:
+            raise ValueError(f"oracle_drag_knn rc={rc}")
+        if cnt.value <= cap:
+            return idx[:cnt.value].copy(), nn[:cnt.value].copy()
+        cap = cnt.value
+
+
 def drag(T, m: int, r: float):
     """All range discords of length m at threshold r (Algorithm 2):
     ascending indices and their nearest-neighbour distances."""
@@ -160,10 +194,11 @@ def interest(heat, minL: int, K: int, exclusive: bool = True):
     return out
 
 
-def merlin(T, minL: int, maxL: int, K: int, exclusive: bool = True, heatmap: bool = False):
+def merlin(T, minL: int, maxL: int, K: int, exclusive: bool = True, heatmap: bool = False, knn: int = 1):
     """MERLIN (Algorithm 1) over lengths minL..maxL.  Returns a dict with
     ``idx`` [L,K], ``nn`` [L,K], ``count`` [L], ``r`` [L], ``calls`` [L] and,
-    when asked, ``heatmap`` [L, n-minL+1]."""
+    when asked, ``heatmap`` [L, n-minL+1].  knn > 1 runs it on the k-th
+    neighbour distance (reading R14) instead of the nearest one."""
     T = _f32(T)
     L = maxL - minL + 1
     out = {
@@ -171,10 +206,10 @@ def merlin(T, minL: int, maxL: int, K: int, exclusive: bool = True, heatmap: boo
         "count": np.empty(L, dtype=np.int64), "r": np.empty(L), "calls": np.empty(L, dtype=np.int32),
     }
     heat = np.empty((L, len(T) - minL + 1), dtype=np.float32) if heatmap else None
-    rc = _load().oracle_merlin(_p(T, _f32p), len(T), minL, maxL, K, int(exclusive),
-                               _p(out["idx"], _i64p), _p(out["nn"], _f64p), _p(out["count"], _i64p),
-                               _p(out["r"], _f64p), _p(out["calls"], _i32p),
-                               _p(heat, _f32p) if heat is not None else None)
+    rc = _load().oracle_merlin_knn(_p(T, _f32p), len(T), minL, maxL, K, int(exclusive), int(knn),
+                                   _p(out["idx"], _i64p), _p(out["nn"], _f64p), _p(out["count"], _i64p),
+                                   _p(out["r"], _f64p), _p(out["calls"], _i32p),
+                                   _p(heat, _f32p) if heat is not None else None)
     if rc:
         raise ValueError(f"oracle_merlin rc={rc}")
     if heat is not None:

@@ -19,7 +19,8 @@
  *   - DRAG, Algorithm 2: phase 1 candidate selection, phase 2 refinement
  *     with the early-abandoning distance of Sec. 2.2;
  *   - MERLIN, Algorithm 1: the r schedule over lengths minL..maxL;
- *   - greedy top-K and the discord heatmap of Eq. 10.
+ *   - greedy top-K and the discord heatmap of Eq. 10;
+ *   - the k-th non-self neighbour variant (reading R14) by brute force.
  *
  * Readings of the paper taken here (the paper is garbled or silent):
  *   R1  r is in distance units; every comparison is d < r on the plain
@@ -49,6 +50,14 @@
  *   R9  Heatmap (Eq. 10): row m, column i holds nnDist^2 / (2m) for the
  *       range discords at the final r of that length and 0 elsewhere; the
  *       row width is n - minL + 1.
+ *   R14 k-th neighbour variant (the top-k discord definition of Sec. 2.1,
+ *       read literally): the k-distance of window i is the k-th smallest
+ *       distance to its non-self matches j (|i - j| >= m), every such j
+ *       counted, so neighbours may overlap one another.  k = 1 is the
+ *       nearest-neighbour distance.  A window with fewer than k non-self
+ *       matches has no k-distance and is never a discord.  The range
+ *       k-discords at r are the windows whose k-distance is >= r; MERLIN
+ *       runs unchanged on the k-distance.
  *   R13 Discord interest (Eq. 11, Sec. 6): the interest of index i is the
  *       largest heatmap value over the lengths, and its length the smallest
  *       m reaching it.  The top-k interesting discords are taken greedily
@@ -178,6 +187,79 @@ int oracle_nn_one(const float *T, int64_t n, int32_t m, int64_t i, double *nn, i
     return 0;
 }
 
+/* ---------- k-th non-self neighbour (reading R14) ---------- */
+
+static int cmp_double(const void *a, const void *b) {
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* knn[i] = the k-th smallest distance from window i to its non-self
+ * matches, by brute force (all distances of the row, sorted); INFINITY when
+ * the window has fewer than k non-self matches. */
+int oracle_knn(const float *T, int64_t n, int32_t m, int32_t k, double *knn) {
+    if (!T || !knn || m < 1 || n < m || k < 1) return -1;
+    int64_t N = n - m + 1;
+    double *mu = (double *)malloc(sizeof(double) * N), *sd = (double *)malloc(sizeof(double) * N);
+    if (!mu || !sd) { free(mu); free(sd); return -2; }
+    oracle_stats(T, n, m, mu, sd);
+    int bad = 0;
+#pragma omp parallel
+    {
+        double *row = (double *)malloc(sizeof(double) * N);
+        if (!row) {
+#pragma omp atomic write
+            bad = 1;
+        }
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < N; ++i) {
+            if (!row) continue;
+            int64_t cnt = 0;
+            for (int64_t j = 0; j < N; ++j) {
+                if (llabs(i - j) < m) continue;
+                row[cnt++] = zdist2(T, m, i, j, mu[i], sd[i], mu[j], sd[j], INFINITY);
+            }
+            if (cnt < k) { knn[i] = INFINITY; continue; }
+            qsort(row, (size_t)cnt, sizeof(double), cmp_double);
+            knn[i] = sqrt(row[k - 1]);
+        }
+        free(row);
+    }
+    free(mu);
+    free(sd);
+    return bad ? -2 : 0;
+}
+
+/* Range k-discords at r (reading R14): the windows whose k-distance is
+ * finite and >= r (every finite one when r <= 0), ascending; up to `cap`
+ * written, *count receives the full number.  `knn` may hold the profile
+ * from oracle_knn, or be NULL to compute it here. */
+int oracle_drag_knn(const float *T, int64_t n, int32_t m, int32_t k, double r, const double *knn,
+                    int64_t *out_idx, double *out_nn, int64_t cap, int64_t *count) {
+    if (!T || m < 1 || n < m || k < 1 || !count) return -1;
+    int64_t N = n - m + 1;
+    double *own = NULL;
+    if (!knn) {
+        own = (double *)malloc(sizeof(double) * N);
+        if (!own) return -2;
+        int rc = oracle_knn(T, n, m, k, own);
+        if (rc) { free(own); return rc; }
+        knn = own;
+    }
+    int64_t c = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (!isfinite(knn[i]) || (r > 0.0 && knn[i] < r)) continue;
+        if (c < cap) {
+            if (out_idx) out_idx[c] = i;
+            if (out_nn) out_nn[c] = knn[i];
+        }
+        ++c;
+    }
+    *count = c;
+    free(own);
+    return 0;
+}
+
 /* ---------- DRAG (Algorithm 2) ---------- */
 
 /* Range discords of length m at threshold r: writes up to `cap` (index,
@@ -279,12 +361,15 @@ int oracle_topk(const int64_t *idx, const double *nn, int64_t count, int32_t m, 
 
 typedef struct {
     int64_t *idx; double *nn; int64_t cap; int64_t count;
+    int32_t knn;           /* k of reading R14 (1: nearest neighbour, DRAG) */
+    const double *prof;    /* k-distances of the current length when knn > 1 */
 } drag_buf;
 
 static int run_drag(const float *T, int64_t n, int32_t m, double r, drag_buf *b) {
     for (;;) {
         int64_t cnt = 0;
-        int rc = oracle_drag(T, n, m, r, b->idx, b->nn, b->cap, &cnt);
+        int rc = b->knn > 1 ? oracle_drag_knn(T, n, m, b->knn, r, b->prof, b->idx, b->nn, b->cap, &cnt)
+                            : oracle_drag(T, n, m, r, b->idx, b->nn, b->cap, &cnt);
         if (rc) return rc;
         if (cnt <= b->cap) { b->count = cnt; return 0; }
         free(b->idx); free(b->nn);
@@ -310,22 +395,33 @@ static int drag_and_pick(const float *T, int64_t n, int32_t m, double r, int32_t
  * out_count: [L] number of range discords at the final r; out_r: [L] final r;
  * out_calls: [L] DRAG calls made; out_heat: [L*(n-minL+1)] or NULL.
  */
-int oracle_merlin(const float *T, int64_t n, int32_t minL, int32_t maxL, int32_t K, int exclusive,
-                  int64_t *out_idx, double *out_nn, int64_t *out_count, double *out_r,
-                  int32_t *out_calls, float *out_heat) {
-    if (!T || minL < 3 || maxL < minL || n < 2 * (int64_t)maxL || K < 1) return -1;
+int oracle_merlin_knn(const float *T, int64_t n, int32_t minL, int32_t maxL, int32_t K, int exclusive,
+                      int32_t knn, int64_t *out_idx, double *out_nn, int64_t *out_count, double *out_r,
+                      int32_t *out_calls, float *out_heat) {
+    if (!T || minL < 3 || maxL < minL || n < 2 * (int64_t)maxL || K < 1 || knn < 1) return -1;
     const int32_t L = maxL - minL + 1;
     const int64_t W = n - minL + 1;
     drag_buf b = {0};
     b.cap = 1024;
+    b.knn = knn;
     b.idx = (int64_t *)malloc(sizeof(int64_t) * b.cap);
     b.nn = (double *)malloc(sizeof(double) * b.cap);
     double *sched = (double *)malloc(sizeof(double) * L); /* nnDist_m fed to the schedule */
-    if (!b.idx || !b.nn || !sched) { free(b.idx); free(b.nn); free(sched); return -2; }
+    /* k-distances of one length: every DRAG call of that length thresholds them */
+    double *prof = knn > 1 ? (double *)malloc(sizeof(double) * (size_t)(n - minL + 1)) : NULL;
+    if (!b.idx || !b.nn || !sched || (knn > 1 && !prof)) {
+        free(b.idx); free(b.nn); free(sched); free(prof);
+        return -2;
+    }
     if (out_heat) memset(out_heat, 0, sizeof(float) * (size_t)L * (size_t)W);
     int rc = 0;
     for (int32_t m = minL; m <= maxL && !rc; ++m) {
         const int32_t l = m - minL;
+        if (knn > 1) {
+            rc = oracle_knn(T, n, m, knn, prof);
+            if (rc) break;
+            b.prof = prof;
+        }
         int64_t *pidx = out_idx + (int64_t)l * K;
         double *pnn = out_nn + (int64_t)l * K;
         int calls = 0, ok = 0;
@@ -375,8 +471,15 @@ int oracle_merlin(const float *T, int64_t n, int32_t minL, int32_t maxL, int32_t
                 row[b.idx[q]] = (float)(b.nn[q] * b.nn[q] / (2.0 * (double)m));
         }
     }
-    free(b.idx); free(b.nn); free(sched);
+    free(b.idx); free(b.nn); free(sched); free(prof);
     return rc;
+}
+
+int oracle_merlin(const float *T, int64_t n, int32_t minL, int32_t maxL, int32_t K, int exclusive,
+                  int64_t *out_idx, double *out_nn, int64_t *out_count, double *out_r,
+                  int32_t *out_calls, float *out_heat) {
+    return oracle_merlin_knn(T, n, minL, maxL, K, exclusive, 1, out_idx, out_nn, out_count, out_r, out_calls,
+                             out_heat);
 }
 
 /* ---------- discord interest across lengths (Eq. 11, reading R13) ---------- */

@@ -374,3 +374,132 @@ def test_interest_top1_is_a_per_length_top1():
     l = int(np.argmax(val))
     assert got["idx"][0] == res["idx"][l, 0]
     assert got["value"][0] == val[l]
+
+
+# ------------------------------------ k-th neighbour variant (reading R14)
+
+def _py_knn(T, m, k):
+    """numpy brute force: z-scores by numpy, every non-self distance of a row
+    sorted; the R2 convention for flat windows; inf where a window has fewer
+    than k non-self matches."""
+    T = np.asarray(T, dtype=np.float64)
+    N = len(T) - m + 1
+    W = np.lib.stride_tricks.sliding_window_view(T, m)
+    mu, sd = W.mean(axis=1), W.std(axis=1)
+    flat = sd <= 2.0 ** -22 * np.abs(mu)
+    Z = (W - mu[:, None]) / np.where(flat, 1.0, sd)[:, None]
+    out = np.full(N, np.inf)
+    for i in range(N):
+        j = np.array([j for j in range(N) if abs(i - j) >= m], dtype=np.int64)
+        if len(j) < k:
+            continue
+        d2 = ((Z[j] - Z[i]) ** 2).sum(axis=1)
+        d2 = np.where(flat[j] & flat[i], 0.0, np.where(flat[j] | flat[i], 2.0 * m, d2))
+        out[i] = math.sqrt(np.sort(d2)[k - 1])
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 7])
+@pytest.mark.parametrize("n,m,seed", [(60, 5, 30), (90, 9, 31)])
+def test_knn_matches_numpy_brute_force(n, m, seed, k):
+    T = _rw(n, seed)
+    np.testing.assert_allclose(oracle.knn_profile(T, m, k), _py_knn(T, m, k), rtol=1e-9, atol=1e-9)
+
+
+def test_knn_with_flat_windows():
+    T = np.concatenate([_rw(40, 32), np.full(20, 2.5), _rw(40, 33)]).astype(np.float32)
+    for k in (1, 3):
+        np.testing.assert_allclose(oracle.knn_profile(T, 6, k), _py_knn(T, 6, k), rtol=1e-9, atol=1e-9)
+
+
+def test_knn_k1_is_the_matrix_profile():
+    T = _rw(400, 34)
+    for m in (6, 25):
+        mp, _ = oracle.matrix_profile(T, m)
+        np.testing.assert_array_equal(oracle.knn_profile(T, m, 1), mp)
+
+
+def test_knn_nondecreasing_in_k():
+    T = _rw(300, 35)
+    prev = oracle.knn_profile(T, 12, 1)
+    for k in range(2, 9):
+        cur = oracle.knn_profile(T, 12, k)
+        assert np.all(cur >= prev)
+        prev = cur
+
+
+def test_knn_exact_copies_closed_form():
+    """A pattern tiled exactly: window i has an exact copy at every non-self
+    j = i (mod p), so its k-distance is 0 for k up to that number of copies
+    and positive beyond it."""
+    p, m = 23, 9
+    T = np.tile(_rw(p, 36), 9).astype(np.float32)
+    N = len(T) - m + 1
+    copies = np.array([sum(1 for j in range(i % p, N, p) if abs(i - j) >= m) for i in range(N)])
+    for k in (1, 2, 5, 8):
+        d = oracle.knn_profile(T, m, k)
+        assert np.all(d[copies >= k] == 0.0)
+        assert np.all(d[copies < k] > 1e-3)
+
+
+def test_knn_fewer_than_k_matches():
+    """n = 2m + 5: the middle windows have few non-self matches; a window
+    with fewer than k has no k-distance and is never a range k-discord."""
+    m = 10
+    T = _rw(2 * m + 5, 37)
+    N = len(T) - m + 1
+    cnt = np.array([sum(1 for j in range(N) if abs(i - j) >= m) for i in range(N)])
+    for k in (1, 2, 3, 6):
+        d = oracle.knn_profile(T, m, k)
+        assert np.array_equal(np.isfinite(d), cnt >= k)
+        idx, _ = oracle.drag_knn(T, m, k, 0.0)
+        assert idx.tolist() == np.nonzero(cnt >= k)[0].tolist()
+
+
+def test_drag_knn_is_the_thresholded_profile():
+    T = _rw(500, 38)
+    m = 15
+    for k in (2, 5):
+        d = oracle.knn_profile(T, m, k)
+        fin = np.isfinite(d)
+        for r in (np.quantile(d[fin], 0.5), np.quantile(d[fin], 0.95), 0.0, -1.0):
+            idx, nn = oracle.drag_knn(T, m, k, r)
+            want = np.nonzero(fin & ((d >= r) | (r <= 0)))[0]
+            assert idx.tolist() == want.tolist()
+            np.testing.assert_array_equal(nn, d[want])
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_merlin_knn_against_brute_force(k):
+    """MERLIN on the k-distance: the picks are greedy top-K over the numpy
+    k-distance profile (the same lemma as for k = 1: the range discords at r
+    are an upper set of the profile), and the count is that of the profile
+    at the final r."""
+    T = _rw(500, 39)
+    minL, maxL, K = 10, 18, 2
+    res = oracle.merlin(T, minL, maxL, K, True, heatmap=True, knn=k)
+    for l, m in enumerate(range(minL, maxL + 1)):
+        d = _py_knn(T, m, k)
+        picks = _greedy(d, m, K, True)
+        assert res["idx"][l].tolist() == picks
+        np.testing.assert_allclose(res["nn"][l], d[picks], rtol=1e-9)
+        r = res["r"][l]
+        assert res["count"][l] == int(np.sum(np.isfinite(d) & (d >= r)))
+
+
+def test_knn_finds_a_twin_anomaly():
+    """Twin freak: a burst that occurs twice hides from the nearest-neighbour
+    distance (each copy matches the other exactly) but not from the second
+    neighbour."""
+    rng = np.random.default_rng(40)
+    p, m = 50, 30
+    x = np.tile(np.sin(2 * np.pi * np.arange(p) / p), 40) + rng.normal(0, 0.02, 40 * p)
+    burst = rng.normal(0, 1, 40)
+    x[600:640] = burst
+    x[1400:1440] = burst
+    x = x.astype(np.float32)
+    d1, d2 = oracle.knn_profile(x, m, 1), oracle.knn_profile(x, m, 2)
+    inside = list(range(600, 611)) + list(range(1400, 1411))  # windows within a copy
+    far = [i for i in range(len(d1)) if not (570 < i < 640 or 1370 < i < 1440)]
+    assert np.all(d1[inside] == 0.0)
+    assert d2[inside].min() > d2[far].max()
