@@ -105,6 +105,14 @@ typedef struct {
                                 as 1 GiB holds); strips past the cap seed on the CUDA cores */
     int32_t refine_seg;      /* columns per refine sweep work item: 0 = automatic (2048 for
                                 passes holding >= 2e6 columns, else 1024), or 1024 / 2048 */
+    int32_t knn_k;           /* k-th neighbour variant (the top-k discord definition of
+                                Sec. 2.1 read literally): 0 or 1 = the nearest non-self
+                                match (DRAG); k in 2..16 = every distance, range test, top-K,
+                                heatmap and schedule value uses the k-th smallest distance
+                                to the non-self matches, every match counted; a window with
+                                fewer than k non-self matches is never a discord.  With
+                                k > 1 no pair prunes (every window is refined over all its
+                                columns), so a call costs a full pass over the pairs. */
 } palmad_options;
 
 /* Per-call counters of the most recent find/drag call. */

@@ -131,16 +131,22 @@ def knn_profile(T, m: int, k: int):
     return out
 
 
-def drag_knn(T, m: int, k: int, r: float):
+def drag_knn(T, m: int, k: int, r: float, profile=None):
     """Range k-discords of length m at threshold r (reading R14): ascending
-    indices and their k-distances."""
+    indices and their k-distances.  `profile` may pass the k-distances from
+    knn_profile(T, m, k) so that they are not recomputed."""
     T = _f32(T)
+    prof = None
+    if profile is not None:
+        prof = np.ascontiguousarray(profile, dtype=np.float64)
+        if len(prof) != len(T) - m + 1:
+            raise ValueError("profile length must be n - m + 1")
     cap = 1024
     while True:
         idx, nn = np.empty(cap, dtype=np.int64), np.empty(cap)
         cnt = ctypes.c_int64(0)
-        rc = _load().oracle_drag_knn(_p(T, _f32p), len(T), m, k, float(r), None, _p(idx, _i64p), _p(nn, _f64p),
-                                     cap, ctypes.byref(cnt))
+        rc = _load().oracle_drag_knn(_p(T, _f32p), len(T), m, k, float(r), _p(prof, _f64p) if prof is not None else None,
+                                     _p(idx, _i64p), _p(nn, _f64p), cap, ctypes.byref(cnt))
         if rc:
             raise ValueError(f"oracle_drag_knn rc={rc}")
         if cnt.value <= cap:

@@ -263,6 +263,7 @@ palmad_status read_options(palmad_ctx* ctx, const palmad_options* in, palmad_opt
     if (o.seed_rows_max < 0) return fail(ctx, PALMAD_ERR_ARG, "seed_rows_max must be >= 0");
     if (o.refine_seg != 0 && o.refine_seg != kRefineSeg && o.refine_seg != kRefineSegLong)
         return fail(ctx, PALMAD_ERR_ARG, "refine_seg must be 0, 1024 or 2048");
+    if (o.knn_k < 0 || o.knn_k > kMaxKnn) return fail(ctx, PALMAD_ERR_ARG, "knn_k must lie in [0, 16]");
     return PALMAD_OK;
 }
 
@@ -349,6 +350,7 @@ Pass base_pass(palmad_ctx* ctx, int nl, int K, bool exclusive, const palmad_opti
     p.nl = nl;
     p.K = K;
     p.exclusive = exclusive ? 1 : 0;
+    p.knn = o.knn_k > 1 ? o.knn_k : 1;
     p.seg = kRefineSeg;
     static_assert(kRefineSeg >= kCoarseMin && kRefineSegLong % kRefineSeg == 0, "segments cover the coarse pool");
     p.cap = o.select_cap > 0 ? o.select_cap : kDefaultCap;
@@ -429,7 +431,12 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
         for (int l = 0; l < nl; ++l) cols += ctx->h_lanes[l].N;
         p.seg = o.refine_seg ? o.refine_seg : (cols >= kLongPass ? kRefineSegLong : kRefineSeg);
     }
-    p.mixed = (o.precision == PALMAD_PREC_MIXED && refine_tc_supported(p)) ? 1 : 0;
+    // The tensor-core direct refine records chunk maxima as upper bounds
+    // (value + eps_j) and only the survivor maximum as a lower bound; the
+    // k-th neighbour re-check needs k columns that reach its threshold, so
+    // that variant refines direct strips on the FP32 form, which records
+    // the FP32 values themselves.
+    p.mixed = (o.precision == PALMAD_PREC_MIXED && p.knn <= 1 && refine_tc_supported(p)) ? 1 : 0;
     p.direct_below = o.direct_below;
     p.strip_row = ctx->strip_row.p;
     p.seed_ngroups = &ctx->small.p->seed_ngroups;
@@ -685,7 +692,8 @@ Lane make_lane(palmad_ctx* ctx, SeriesJob& s, int32_t li, double r, const palmad
     L.didx = S.didx.p;
     L.dnn = S.dnn.p;
     L.r = r;
-    L.prune = r > 0.0 ? 1 : 0;
+    // k-th neighbour variant: no single pair decides, every window is refined
+    L.prune = (r > 0.0 && o.knn_k <= 1) ? 1 : 0;
     L.rho_thr = float(1.0 - r * r / (2.0 * L.m));
     L.band = float(o.band_rel * r * r / L.m);
     // statistics source
@@ -1310,7 +1318,7 @@ palmad_status palmad_drag(palmad_ctx* ctx, const float* T, int64_t n, int32_t m,
     L.mu_src = S.mu.p;
     L.var_src = S.var.p;
     L.r = r;
-    L.prune = r > 0.0 ? 1 : 0;
+    L.prune = (r > 0.0 && o.knn_k <= 1) ? 1 : 0;
     L.rho_thr = float(1.0 - r * r / (2.0 * m));
     L.band = float(o.band_rel * r * r / m);
     req[0].state = LaneState{};

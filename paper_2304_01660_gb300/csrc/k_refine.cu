@@ -22,6 +22,9 @@
 //                 FP32 rho lies within 2 eps of its FP32 maximum (a set that
 //                 provably holds the true nearest neighbour) is recomputed in
 //                 FP64 (Eq. 4-5 directly), and the minimum FP64 d^2 kept.
+//                 In the k-th neighbour variant the threshold comes from the
+//                 k-th largest coarse maximum and the k-th smallest d^2 is
+//                 kept.
 #include "palmad_dev.cuh"
 
 namespace palmad {
@@ -331,9 +334,46 @@ __device__ __forceinline__ bool is_flat_var(double mu, double var) {
 // column within 2 eps of the FP32 maximum in FP64 with the m terms split
 // over the lanes; the survivor's z-normalised FP64 window is staged once in
 // the warp's shared memory.
+constexpr double kInfD = __builtin_huge_val();
 constexpr int kRecheckWarps = 8;
 constexpr int kRecheckWin = 512;    // survivor windows up to this length use shared memory
 
+// k-th largest of n encoded (order-preserving) coarse maxima, by at most k
+// rounds of a warp maximum below the previous one; 0 (below every encoded
+// float) when fewer than k values exist.
+__device__ uint32_t kth_largest_enc(const uint32_t* __restrict__ c2, int32_t n, int32_t k, int lane) {
+    unsigned long long cur = 0x100000000ull;  // exclusive upper bound of this round
+    for (int t = 0; t < k; ++t) {
+        uint32_t mx = 0;
+        bool any = false;
+        for (int32_t q = lane; q < n; q += 32) {
+            const uint32_t v = c2[q];
+            if (v < cur) {
+                mx = v > mx ? v : mx;
+                any = true;
+            }
+        }
+        mx = __reduce_max_sync(kFull, mx);
+        if (!__any_sync(kFull, any)) return 0u;
+        uint32_t cnt = 0;
+        for (int32_t q = lane; q < n; q += 32) cnt += c2[q] >= mx ? 1u : 0u;
+        cnt = __reduce_add_sync(kFull, cnt);
+        if (cnt >= uint32_t(k)) return mx;
+        cur = mx;
+    }
+    return 0u;
+}
+
+// KNN: the k-th neighbour variant (p.knn = k > 1).  The row's threshold is
+// the k-th largest coarse maximum minus 2 eps: at least k columns reach that
+// maximum in FP32, so the k-th largest FP64 rho is at least it minus eps, and
+// every column among the k nearest in FP64 is at least it minus 2 eps in
+// FP32.  When fewer than k coarse blocks hold a non-self column the row is
+// re-checked over every non-self column.  The k smallest FP64 distances are
+// kept sorted in registers (identical in every lane of the warp) and the k-th
+// becomes the survivor's distance; with fewer than k it stays infinite, so
+// the window is not a discord.
+template <bool KNN>
 __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
     __shared__ double zc_all[kRecheckWarps][kRecheckWin];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -353,9 +393,20 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
         const int64_t N = L.N;
         const float* T = L.T;
         const WinRec* win = L.win;
-        const float gm = dec_f32(__ldcg(&p.gmax[g]));
-        const float thr = gm - 2.f * eps_bound(m, S);
+        const uint32_t* c2 = p.cmax2 + g * int64_t(p.ncoarse_max);
+        const int32_t ncoarse = int32_t((N + p.seg - 1) / p.seg);
+        float thr;
+        if (KNN) {
+            const uint32_t ek = kth_largest_enc(c2, ncoarse, p.knn, lane);
+            thr = ek >= enc_f32(-3.402823466e38f) ? dec_f32(ek) - 2.f * eps_bound(m, S) : -kInf;
+        } else {
+            const float gm = dec_f32(__ldcg(&p.gmax[g]));
+            thr = gm - 2.f * eps_bound(m, S);
+        }
         const uint32_t thr_enc = enc_f32(thr);
+        double best[KNN ? kMaxKnn : 1];
+#pragma unroll
+        for (int t = 0; t < (KNN ? kMaxKnn : 1); ++t) best[t] = kInfD;
         const bool has_flat = (S.flags & 2) != 0;
         const float invc = win[c].z;
         const double muc = L.mu[c], varc = L.var[c];
@@ -367,9 +418,7 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
         __syncwarp();
         const float* arow = p.acen + g * int64_t(p.kpad_max);
         const float* cm = p.cmax + g * int64_t(p.nchunks_max);
-        const uint32_t* c2 = p.cmax2 + g * int64_t(p.ncoarse_max);
         const int32_t nchunks = int32_t((N + 31) / 32);
-        const int32_t ncoarse = int32_t((N + p.seg - 1) / p.seg);
         const int32_t cpb = p.seg / 32;  // chunks per coarse block
         for (int32_t cb = 0; cb < ncoarse; cb += 32) {
             const int32_t q2l = cb + lane;
@@ -387,14 +436,15 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
                     // FP32 rho of the chunk's columns, one per lane
                     const int64_t j = int64_t(qq) * 32 + lane;
                     float rho32 = -kInf;
-                    if (j < N && (j - c >= m || c - j >= m)) {
+                    const bool valid = j < N && (j - c >= m || c - j >= m);
+                    if (valid) {
                         const float4 rj = win[j];
                         float acc = 0.f;
                         for (int k = 0; k < m; ++k) acc = fmaf(arow[k], T[j + k] - rj.w, acc);
                         rho32 = acc * invc * rj.z;
                         if (has_flat && (invc == 0.f || rj.z == 0.f)) rho32 = (invc == 0.f && rj.z == 0.f) ? 1.f : 0.f;
                     }
-                    uint32_t bc = __ballot_sync(kFull, rho32 >= thr);
+                    uint32_t bc = __ballot_sync(kFull, valid && rho32 >= thr);
                     while (bc) {
                         const int cl = __ffs(bc) - 1;
                         bc &= bc - 1;
@@ -418,8 +468,20 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
 #pragma unroll
                             for (int o = 16; o >= 1; o >>= 1) d2 += __shfl_xor_sync(kFull, d2, o);
                         }
+                        if (KNN) {
+                            // sorted insertion into the k smallest (uniform over the warp)
+                            double v = d2;
+#pragma unroll
+                            for (int t = 0; t < (KNN ? kMaxKnn : 1); ++t)
+                                if (t < p.knn && v < best[t]) {
+                                    const double w = best[t];
+                                    best[t] = v;
+                                    v = w;
+                                }
+                        }
                         if (lane == 0) {
-                            atomicMin(&p.nn2[g], static_cast<unsigned long long>(__double_as_longlong(d2)));
+                            if (!KNN)
+                                atomicMin(&p.nn2[g], static_cast<unsigned long long>(__double_as_longlong(d2)));
                             atomicMax(&S.maxerr, enc_f32(fabsf(rc32 - float(1.0 - d2 / (2.0 * m)))));
                             ++fp64;
                         }
@@ -427,6 +489,14 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
                 }
                 }
             }
+        }
+        if (KNN && lane == 0) {
+            // the k-th smallest (infinite when fewer than k non-self columns)
+            double kth = best[0];
+#pragma unroll
+            for (int t = 0; t < (KNN ? kMaxKnn : 1); ++t)
+                if (t == p.knn - 1) kth = best[t];
+            p.nn2[g] = static_cast<unsigned long long>(__double_as_longlong(kth));
         }
         __syncwarp();
     }
@@ -461,7 +531,8 @@ cudaError_t launch_refine_direct(const Pass& p, int grid, cudaStream_t s) {
 
 cudaError_t launch_recheck(const Pass& p, int grid, cudaStream_t s) {
     if (p.nslots <= 0) return cudaSuccess;
-    k_recheck<<<grid, kRecheckWarps * 32, 0, s>>>(p);
+    if (p.knn > 1) k_recheck<true><<<grid, kRecheckWarps * 32, 0, s>>>(p);
+    else k_recheck<false><<<grid, kRecheckWarps * 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 

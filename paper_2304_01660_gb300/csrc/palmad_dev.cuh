@@ -26,6 +26,7 @@ constexpr int kCoarseMin = 1024;  // smallest coarse block of the chunk maxima (
 constexpr int kSelPieceCols = 512;       // columns per select work item (a strip's scan is cut into pieces)
 constexpr int kSelPieceColsShort = 256;  // the same for passes with too few strips to fill the GPU
 constexpr int kMaxK = 1024;    // largest top-K
+constexpr int kMaxKnn = 16;    // largest k of the k-th neighbour variant
 
 // Per-window data the FP32 kernels read, one 16-byte record per window:
 //   x = df_i = (t[i+m-1] - t[i-1]) / 2          (Eq. 9 diagonal update)
@@ -113,6 +114,7 @@ struct Pass {
     int64_t sel_items;     // total select strips
     int32_t sel_pieces;    // column pieces per select strip
     int32_t sel_cols;      // columns per select piece (multiple of 32)
+    int32_t knn;           // k-th neighbour distance (1: nearest neighbour)
     int32_t direct_below;  // > 0: strips with fewer survivors take the direct form
     int64_t nmax;          // largest N over the lanes
     // refine pool (this round)

@@ -45,6 +45,7 @@ class Options(ctypes.Structure):
         ("tc_seed_min", ctypes.c_int32),
         ("seed_rows_max", ctypes.c_int32),
         ("refine_seg", ctypes.c_int32),
+        ("knn_k", ctypes.c_int32),
     ]
 
 

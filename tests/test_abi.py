@@ -59,11 +59,11 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "palmad.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(palmad_options), offsetof(palmad_options, band_rel),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(palmad_options), offsetof(palmad_options, band_rel),
          offsetof(palmad_options, profile), sizeof(palmad_stats), offsetof(palmad_stats, max_fp32_rho_err),
          offsetof(palmad_stats, kernel_ms), offsetof(palmad_stats, refine_flops),
          offsetof(palmad_options, direct_below), offsetof(palmad_options, refine_seg),
-         offsetof(palmad_stats, seed_flops));
+         offsetof(palmad_stats, seed_flops), offsetof(palmad_options, knn_k));
   return 0;
 }
 """)
@@ -73,7 +73,7 @@ int main(void) {
     O, S = palmad.Options, palmad.Stats
     assert got == [ctypes.sizeof(O), O.band_rel.offset, O.profile.offset, ctypes.sizeof(S),
                    S.max_fp32_rho_err.offset, S.kernel_ms.offset, S.refine_flops.offset,
-                   O.direct_below.offset, O.refine_seg.offset, S.seed_flops.offset]
+                   O.direct_below.offset, O.refine_seg.offset, S.seed_flops.offset, O.knn_k.offset]
 
 
 def test_create_without_gpu_fails_cleanly(lib):

@@ -503,3 +503,13 @@ def test_knn_finds_a_twin_anomaly():
     far = [i for i in range(len(d1)) if not (570 < i < 640 or 1370 < i < 1440)]
     assert np.all(d1[inside] == 0.0)
     assert d2[inside].min() > d2[far].max()
+
+
+def test_drag_knn_with_a_given_profile():
+    T = _rw(300, 41)
+    d = oracle.knn_profile(T, 12, 3)
+    r = float(np.quantile(d, 0.8))
+    a = oracle.drag_knn(T, 12, 3, r)
+    b = oracle.drag_knn(T, 12, 3, r, d)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
