@@ -277,7 +277,7 @@ palmad_status palmad_topk_profile_noalloc(const double *nn_dev, int64_t N, int32
                                           int64_t *out_count_dev, void *cuda_stream);
 
 /*
- * The most interesting discords across lengths (Eq. 11, Sec. 6), from a
+ * The most interesting discords across lengths (Eq. 11, Sec. 5), from a
  * discord heatmap the caller holds on the device (the out_heatmap_dev of
  * palmad_find_discords_device, Eq. 10).  No allocation, no context.
  *   heat_dev       [L * W] float32, row l = length minL + l (device).

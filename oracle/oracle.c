@@ -58,7 +58,7 @@
  *       matches has no k-distance and is never a discord.  The range
  *       k-discords at r are the windows whose k-distance is >= r; MERLIN
  *       runs unchanged on the k-distance.
- *   R13 Discord interest (Eq. 11, Sec. 6): the interest of index i is the
+ *   R13 Discord interest (Eq. 11, Sec. 5): the interest of index i is the
  *       largest heatmap value over the lengths, and its length the smallest
  *       m reaching it.  The top-k interesting discords are taken greedily
  *       by (interest desc, index asc) among indices of positive interest;

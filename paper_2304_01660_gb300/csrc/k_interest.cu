@@ -1,5 +1,5 @@
 // palmad_discord_interest: the most interesting discords across lengths
-// (Eq. 11, Sec. 6).  The interest of index i is the largest discord-heatmap
+// (Eq. 11, Sec. 5).  The interest of index i is the largest discord-heatmap
 // value over the lengths (Eq. 10: nnDist^2 / (2m) at the range discords of
 // length m, 0 elsewhere) and its length the smallest m reaching it; the
 // top-K interesting discords are taken greedily by (interest desc, index
