@@ -44,6 +44,13 @@ def test_default_options_and_version(lib):
     o = palmad.palmad_default_options()
     assert o.struct_size == ctypes.sizeof(palmad.Options)
     assert o.exclusive_topk == 1 and o.band_rel == pytest.approx(1e-3)
+    # the documented defaults: FP32, plain form, automatic caps and segments,
+    # nearest-neighbour distance
+    assert (o.precision, o.batch_lengths, o.select_cap, o.pool_slots, o.refine_seg, o.knn_k) == (0, 0, 0, 0, 0, 0)
+    assert (o.direct_below, o.tc_seed_min, o.seed_rows_max, o.profile) == (0, 0, 0, 0)
+    assert palmad.palmad_default_options(knn_k=3, batch_lengths=16).knn_k == 3
+    with pytest.raises(KeyError):
+        palmad.palmad_default_options(no_such_option=1)
     assert lib.palmad_default_options(None) == -1
     assert "sm_103a" in palmad.palmad_version()
 
