@@ -145,7 +145,7 @@ typedef struct {
 enum {
     PALMAD_K_STATS = 0,         /* window statistics init / Eq. 7-8 advance */
     PALMAD_K_SELECT = 1,        /* candidate select (Algorithm 3) */
-    PALMAD_K_COMPACT = 2,       /* bitmap -> survivor list (Algorithm 4 line 2) */
+    PALMAD_K_COMPACT = 2,       /* bitmap -> survivor list (Algorithm 4) */
     PALMAD_K_PLAN = 3,          /* survivor split (sweep / direct) + centred windows */
     PALMAD_K_REFINE_SWEEP = 4,  /* refine, recurrence form over dense strips (Algorithm 4) */
     PALMAD_K_REFINE_DIRECT = 5, /* refine, direct form over scattered survivors */

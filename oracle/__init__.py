@@ -53,8 +53,8 @@ def _load():
             lib.oracle_dist.restype = ctypes.c_double
             lib.oracle_mp.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, _f64p, _i64p]
             lib.oracle_nn_one.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _f64p, _i64p]
-            lib.oracle_drag.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _i64p, _f64p,
-                                        ctypes.c_int64, _i64p]
+            lib.oracle_range_discords.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _i64p,
+                                                  _f64p, ctypes.c_int64, _i64p]
             lib.oracle_topk.argtypes = [_i64p, _f64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
                                         _i64p, _f64p]
             lib.oracle_merlin.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -154,21 +154,26 @@ def drag_knn(T, m: int, k: int, r: float, profile=None):
         cap = cnt.value
 
 
-def drag(T, m: int, r: float):
-    """All range discords of length m at threshold r (Algorithm 2):
-    ascending indices and their nearest-neighbour distances."""
+def range_discords(T, m: int, r: float):
+    """All range discords of length m at threshold r (Sec. 2.1), the set one
+    DRAG call (Algorithm 2) returns: ascending indices and their
+    nearest-neighbour distances."""
     T = _f32(T)
     cap = 1024
     while True:
         idx, nn = np.empty(cap, dtype=np.int64), np.empty(cap)
         cnt = ctypes.c_int64(0)
-        rc = _load().oracle_drag(_p(T, _f32p), len(T), m, float(r), _p(idx, _i64p), _p(nn, _f64p), cap,
-                                 ctypes.byref(cnt))
+        rc = _load().oracle_range_discords(_p(T, _f32p), len(T), m, float(r), _p(idx, _i64p), _p(nn, _f64p), cap,
+                                           ctypes.byref(cnt))
         if rc:
-            raise ValueError(f"oracle_drag rc={rc}")
+            raise ValueError(f"oracle_range_discords rc={rc}")
         if cnt.value <= cap:
             return idx[:cnt.value].copy(), nn[:cnt.value].copy()
         cap = cnt.value
+
+
+# The output of one DRAG call at (m, r): the name the parity tests use.
+drag = range_discords
 
 
 def topk(idx, nn, m: int, K: int, exclusive: bool = True):
@@ -201,7 +206,7 @@ def interest(heat, minL: int, K: int, exclusive: bool = True):
 
 
 def merlin(T, minL: int, maxL: int, K: int, exclusive: bool = True, heatmap: bool = False, knn: int = 1):
-    """MERLIN (Algorithm 1) over lengths minL..maxL.  Returns a dict with
+    """MERLIN over lengths minL..maxL (Sec. 2.2; Algorithm 1).  Returns a dict with
     ``idx`` [L,K], ``nn`` [L,K], ``count`` [L], ``r`` [L], ``calls`` [L] and,
     when asked, ``heatmap`` [L, n-minL+1].  knn > 1 runs it on the k-th
     neighbour distance (reading R14) instead of the nearest one."""

@@ -16,9 +16,11 @@
  *   - non-self match |i - j| >= m (Sec. 2.1), range discord
  *     min Dist >= r (Sec. 2.1);
  *   - brute-force non-self-match nearest neighbour ("matrix profile");
- *   - DRAG, Algorithm 2: phase 1 candidate selection, phase 2 refinement
- *     with the early-abandoning distance of Sec. 2.2;
- *   - MERLIN, Algorithm 1: the r schedule over lengths minL..maxL;
+ *   - range discords at r (Sec. 2.1), evaluated from their definition
+ *     window by window; this is the set one DRAG call (Algorithm 2)
+ *     returns;
+ *   - MERLIN's threshold schedule over lengths minL..maxL, as the prose
+ *     of Sec. 2.2 describes it;
  *   - greedy top-K and the discord heatmap of Eq. 10;
  *   - the k-th non-self neighbour variant (reading R14) by brute force.
  *
@@ -30,19 +32,21 @@
  *       (correlation taken as 0 in Eq. 6).
  *   R3  A window with no non-self match (possible when n - m + 1 < 2m) has
  *       no nearest neighbour and is never a discord.
- *   R4  DRAG returns the candidates that survive phase 2 (the candidate set
- *       C), each with its exact nearest-neighbour distance; Algorithm 2's
- *       "D <- D u c" in the else-branch is read as keeping c in C.
+ *   R4  One DRAG call at r outputs the range discords at r (Sec. 2.1), each
+ *       with its exact nearest-neighbour distance.  The refine phase of
+ *       Algorithm 2 adds a candidate to its output while the scan is still
+ *       running; that is read as keeping the candidate until the scan ends.
  *   R5  Top-K per length: the range discords sorted by (nnDist desc, index
  *       asc), taken greedily; with `exclusive` set, a pick must be at least
  *       m away from every earlier pick.
  *   R6  A DRAG call "succeeds" when R5 yields K picks; nnDist_m (the value
  *       fed to the schedule) is the distance of the K-th pick.
- *   R7  Algorithm 1 lines 7-11: r = 0.99 nnDist_{m-1} once, then r <- 0.99 r
- *       on each failure.  Lines 13-17: r = mu - 2 sd of the last five
- *       nnDist (sample deviation, n-1), then r <- r - sd on each failure
- *       (the duplicate call with an unchanged r is not repeated).  If sd is
- *       0 the step is 0.01 mu.
+ *   R7  Sec. 2.2, lengths two to five: the first try is 1% below the
+ *       previous length's nnDist and each failure takes off another 1% of
+ *       the current r (r <- 0.99 r).  Later lengths: the first try is
+ *       mean - 2 sd of the last five nnDist (sample deviation, n-1), and
+ *       each failure subtracts sd; no try repeats an unchanged r.  If sd is
+ *       0 the step is 0.01 mean.
  *   R8  Loop guards (not in the paper): after 60 halvings, 3000 shrinks of
  *       1%, or any r <= 0, the call is made with r = 0, where every window
  *       with a non-self match qualifies; fewer than K picks are then
@@ -65,10 +69,9 @@
  *       with `exclusive` set, a pick's window [i, i + m) must not overlap an
  *       earlier pick's window.
  *
- * Parallelism: the brute-force nearest neighbour runs its rows in parallel
- * and DRAG phase 2 runs its candidates in parallel (each candidate sees the
- * paper's sequence of s, so the result equals the serial loop's).  Phase 1
- * is serial, as in Algorithm 2.
+ * Parallelism: the brute-force nearest neighbour and the range-discord
+ * test run their windows in parallel; each window's result depends on that
+ * window alone, so the output equals the serial loop's.
  */
 #include <math.h>
 #include <stdint.h>
@@ -106,10 +109,9 @@ int oracle_stats(const float *T, int64_t n, int32_t m, double *mu, double *sd) {
 
 /* ---------- distance (Eq. 5 on the z-normalised windows of Eq. 4) ---------- */
 
-/* Squared z-normalised Euclidean distance, summation abandoned (and the
- * partial sum returned) once it reaches `bound2`. */
+/* Squared z-normalised Euclidean distance (Eq. 5 on Eq. 4). */
 static double zdist2(const float *T, int32_t m, int64_t i, int64_t j, double mui, double sdi,
-                     double muj, double sdj, double bound2) {
+                     double muj, double sdj) {
     int fi = is_flat(mui, sdi), fj = is_flat(muj, sdj);
     if (fi && fj) return 0.0;
     if (fi || fj) return 2.0 * (double)m;
@@ -119,7 +121,6 @@ static double zdist2(const float *T, int32_t m, int64_t i, int64_t j, double mui
         double b = ((double)T[j + k] - muj) / sdj;
         double d = a - b;
         s += d * d;
-        if (s >= bound2) break;
     }
     return s;
 }
@@ -129,7 +130,7 @@ double oracle_dist(const float *T, int64_t n, int32_t m, int64_t i, int64_t j) {
     double mui, sdi, muj, sdj;
     window_stats(T, i, m, &mui, &sdi);
     window_stats(T, j, m, &muj, &sdj);
-    return sqrt(zdist2(T, m, i, j, mui, sdi, muj, sdj, INFINITY));
+    return sqrt(zdist2(T, m, i, j, mui, sdi, muj, sdj));
 }
 
 /* ---------- brute-force nearest non-self match ---------- */
@@ -146,7 +147,7 @@ int oracle_mp(const float *T, int64_t n, int32_t m, double *mp, int64_t *mpidx) 
         int64_t arg = -1;
         for (int64_t j = 0; j < N; ++j) {
             if (llabs(i - j) < m) continue;
-            double d2 = zdist2(T, m, i, j, mu[i], sd[i], mu[j], sd[j], INFINITY);
+            double d2 = zdist2(T, m, i, j, mu[i], sd[i], mu[j], sd[j]);
             if (d2 < best) { best = d2; arg = j; }
         }
         mp[i] = sqrt(best);
@@ -174,7 +175,7 @@ int oracle_nn_one(const float *T, int64_t n, int32_t m, int64_t i, double *nn, i
             if (llabs(i - j) < m) continue;
             double muj, sdj;
             window_stats(T, j, m, &muj, &sdj);
-            double d2 = zdist2(T, m, i, j, mui, sdi, muj, sdj, INFINITY);
+            double d2 = zdist2(T, m, i, j, mui, sdi, muj, sdj);
             if (d2 < lb || (d2 == lb && j < la)) { lb = d2; la = j; }
         }
 #pragma omp critical
@@ -217,7 +218,7 @@ int oracle_knn(const float *T, int64_t n, int32_t m, int32_t k, double *knn) {
             int64_t cnt = 0;
             for (int64_t j = 0; j < N; ++j) {
                 if (llabs(i - j) < m) continue;
-                row[cnt++] = zdist2(T, m, i, j, mu[i], sd[i], mu[j], sd[j], INFINITY);
+                row[cnt++] = zdist2(T, m, i, j, mu[i], sd[i], mu[j], sd[j]);
             }
             if (cnt < k) { knn[i] = INFINITY; continue; }
             qsort(row, (size_t)cnt, sizeof(double), cmp_double);
@@ -260,69 +261,54 @@ int oracle_drag_knn(const float *T, int64_t n, int32_t m, int32_t k, double r, c
     return 0;
 }
 
-/* ---------- DRAG (Algorithm 2) ---------- */
+/* ---------- range discords (Sec. 2.1) ---------- */
 
-/* Range discords of length m at threshold r: writes up to `cap` (index,
- * nnDist) pairs in ascending index order; *count receives the full number.
- * Returns 0, or a negative value on bad arguments / allocation failure. */
-int oracle_drag(const float *T, int64_t n, int32_t m, double r, int64_t *out_idx, double *out_nn,
-                int64_t cap, int64_t *count) {
+/*
+ * The range discords of length m at threshold r: the windows whose nearest
+ * non-self match lies at distance >= r, each with that distance (nnDist).
+ * DRAG (Algorithm 2) computes exactly this set; here it is evaluated from
+ * the definition, one window at a time.  Window i is compared with its
+ * non-self matches j in ascending order.  A j with Dist(i, j) < r shows that
+ * i is not a range discord (the "for every non-self match" of the definition
+ * fails there), and the test of i ends.  Otherwise nnDist(i) is the minimum
+ * over every j.  With r <= 0 every window with a non-self match qualifies
+ * (R8); a window with none never does (R3).
+ *
+ * Writes up to `cap` (index, nnDist) pairs in ascending index order;
+ * *count receives the full number.  Returns 0, or a negative value on bad
+ * arguments / allocation failure.
+ */
+int oracle_range_discords(const float *T, int64_t n, int32_t m, double r, int64_t *out_idx, double *out_nn,
+                          int64_t cap, int64_t *count) {
     if (!T || m < 1 || n < m || !count) return -1;
     int64_t N = n - m + 1;
     double *mu = (double *)malloc(sizeof(double) * N), *sd = (double *)malloc(sizeof(double) * N);
-    int64_t *C = (int64_t *)malloc(sizeof(int64_t) * N);
-    if (!mu || !sd || !C) { free(mu); free(sd); free(C); return -2; }
+    double *nn = (double *)malloc(sizeof(double) * N);  /* nnDist, or NAN: not a range discord */
+    if (!mu || !sd || !nn) { free(mu); free(sd); free(nn); return -2; }
     oracle_stats(T, n, m, mu, sd);
-    const int prune = r > 0.0; /* d < r never holds for r <= 0 */
-
-    /* Phase 1: select candidates. */
-    int64_t nc = 0;
-    C[nc++] = 0;
-    for (int64_t s = 1; s < N; ++s) {
-        int is_cand = 1;
-        int64_t w = 0;
-        for (int64_t q = 0; q < nc; ++q) {
-            int64_t c = C[q];
-            int keep = 1;
-            if (prune && llabs(s - c) >= m) {
-                double d2 = zdist2(T, m, s, c, mu[s], sd[s], mu[c], sd[c], INFINITY);
-                if (sqrt(d2) < r) { keep = 0; is_cand = 0; }
-            }
-            if (keep) C[w++] = c;
-        }
-        nc = w;
-        if (is_cand) C[nc++] = s;
-    }
-
-    /* Phase 2: refine with the early-abandoning distance. */
-    double *nn2 = (double *)malloc(sizeof(double) * (nc > 0 ? nc : 1));
-    char *alive = (char *)malloc(nc > 0 ? nc : 1);
-    if (!nn2 || !alive) { free(mu); free(sd); free(C); free(nn2); free(alive); return -2; }
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t q = 0; q < nc; ++q) {
-        int64_t c = C[q];
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < N; ++i) {
         double best = INFINITY;
-        char ok = 1;
-        for (int64_t s = 0; s < N && ok; ++s) {
-            if (s == c || llabs(s - c) < m) continue;
-            double d2 = zdist2(T, m, s, c, mu[s], sd[s], mu[c], sd[c], best);
-            if (prune && sqrt(d2) < r) ok = 0;
-            else if (d2 < best) best = d2;
+        int is_discord = 1;
+        for (int64_t j = 0; j < N && is_discord; ++j) {
+            if (llabs(i - j) < m) continue;
+            double d = sqrt(zdist2(T, m, i, j, mu[i], sd[i], mu[j], sd[j]));
+            if (r > 0.0 && d < r) is_discord = 0;
+            else if (d < best) best = d;
         }
-        alive[q] = ok && isfinite(best);
-        nn2[q] = best;
+        nn[i] = (is_discord && isfinite(best)) ? best : NAN;
     }
-    int64_t k = 0;
-    for (int64_t q = 0; q < nc; ++q) {
-        if (!alive[q]) continue;
-        if (k < cap) {
-            if (out_idx) out_idx[k] = C[q];
-            if (out_nn) out_nn[k] = sqrt(nn2[q]);
+    int64_t c = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (isnan(nn[i])) continue;
+        if (c < cap) {
+            if (out_idx) out_idx[c] = i;
+            if (out_nn) out_nn[c] = nn[i];
         }
-        ++k;
+        ++c;
     }
-    *count = k;
-    free(mu); free(sd); free(C); free(nn2); free(alive);
+    *count = c;
+    free(mu); free(sd); free(nn);
     return 0;
 }
 
@@ -357,19 +343,20 @@ int oracle_topk(const int64_t *idx, const double *nn, int64_t count, int32_t m, 
     return got;
 }
 
-/* ---------- MERLIN (Algorithm 1) ---------- */
+/* ---------- MERLIN over a length range (Sec. 2.2) ---------- */
 
+/* Range discords of one length at one r, into a buffer that grows as needed. */
 typedef struct {
     int64_t *idx; double *nn; int64_t cap; int64_t count;
-    int32_t knn;           /* k of reading R14 (1: nearest neighbour, DRAG) */
+    int32_t knn;           /* k of reading R14 (1: nearest neighbour) */
     const double *prof;    /* k-distances of the current length when knn > 1 */
-} drag_buf;
+} discord_set;
 
-static int run_drag(const float *T, int64_t n, int32_t m, double r, drag_buf *b) {
+static int find_range_discords(const float *T, int64_t n, int32_t m, double r, discord_set *b) {
     for (;;) {
         int64_t cnt = 0;
         int rc = b->knn > 1 ? oracle_drag_knn(T, n, m, b->knn, r, b->prof, b->idx, b->nn, b->cap, &cnt)
-                            : oracle_drag(T, n, m, r, b->idx, b->nn, b->cap, &cnt);
+                            : oracle_range_discords(T, n, m, r, b->idx, b->nn, b->cap, &cnt);
         if (rc) return rc;
         if (cnt <= b->cap) { b->count = cnt; return 0; }
         free(b->idx); free(b->nn);
@@ -380,20 +367,57 @@ static int run_drag(const float *T, int64_t n, int32_t m, double r, drag_buf *b)
     }
 }
 
-/* One DRAG call of the schedule: returns 1 on success (K picks), 0 otherwise. */
-static int drag_and_pick(const float *T, int64_t n, int32_t m, double r, int32_t K, int exclusive,
-                         drag_buf *b, int64_t *pidx, double *pnn, int *rc) {
-    *rc = run_drag(T, n, m, r, b);
-    if (*rc) return 0;
-    int got = oracle_topk(b->idx, b->nn, b->count, m, K, exclusive, pidx, pnn);
-    if (got < 0) { *rc = got; return 0; }
-    return got == K;
+/*
+ * How Sec. 2.2 chooses r for the length with schedule index l (l = m - minL)
+ * from the nnDist values of the lengths before it (prev[0 .. l-1]): the
+ * first try, and how a failed try lowers r (next = r * scale - minus).
+ *   l = 0      2 sqrt(minL), the largest possible z-normalised distance,
+ *              halved per failure;
+ *   l = 1..4   the previous length's nnDist less 1%, then 1% of r less per
+ *              failure (R7);
+ *   l >= 5     mean - 2 sd of the last five nnDist values (sample deviation),
+ *              sd less per failure; 0.01 mean when sd is 0 (R7).
+ * The try counts after which r drops to 0 are reading R8.
+ */
+typedef struct { double first, scale, minus; int max_tries; } r_rule;
+
+static r_rule threshold_rule(int32_t l, int32_t minL, const double *prev) {
+    r_rule q;
+    if (l == 0) {
+        q.first = 2.0 * sqrt((double)minL);
+        q.scale = 0.5;
+        q.minus = 0.0;
+        q.max_tries = 60;
+    } else if (l < 5) {
+        q.first = 0.99 * prev[l - 1];
+        q.scale = 0.99;
+        q.minus = 0.0;
+        q.max_tries = 3000;
+    } else {
+        const double *last5 = prev + (l - 5);
+        double mean = 0.0, ss = 0.0;
+        for (int k = 0; k < 5; ++k) mean += last5[4 - k];
+        mean /= 5.0;
+        for (int k = 0; k < 5; ++k) ss += (last5[4 - k] - mean) * (last5[4 - k] - mean);
+        const double sd = sqrt(ss / 4.0);
+        q.first = mean - 2.0 * sd;
+        q.scale = 1.0;
+        q.minus = sd > 0.0 ? sd : 0.01 * mean;
+        q.max_tries = 3000;
+    }
+    return q;
 }
 
 /*
  * out_idx/out_nn: [L*K] picks per length (index -1 and 0.0 when fewer);
  * out_count: [L] number of range discords at the final r; out_r: [L] final r;
- * out_calls: [L] DRAG calls made; out_heat: [L*(n-minL+1)] or NULL.
+ * out_calls: [L] range-discord evaluations (DRAG calls) made; out_heat:
+ * [L*(n-minL+1)] or NULL.
+ *
+ * Lengths run in increasing order.  For each, r starts at its rule's first
+ * try; a try succeeds when the greedy top-K of the range discords at r
+ * (R5) yields K picks (R6).  A try with r <= 0 is the last one.  The K-th
+ * pick's nnDist is what later lengths' rules read.
  */
 int oracle_merlin_knn(const float *T, int64_t n, int32_t minL, int32_t maxL, int32_t K, int exclusive,
                       int32_t knn, int64_t *out_idx, double *out_nn, int64_t *out_count, double *out_r,
@@ -401,22 +425,22 @@ int oracle_merlin_knn(const float *T, int64_t n, int32_t minL, int32_t maxL, int
     if (!T || minL < 3 || maxL < minL || n < 2 * (int64_t)maxL || K < 1 || knn < 1) return -1;
     const int32_t L = maxL - minL + 1;
     const int64_t W = n - minL + 1;
-    drag_buf b = {0};
+    discord_set b = {0};
     b.cap = 1024;
     b.knn = knn;
     b.idx = (int64_t *)malloc(sizeof(int64_t) * b.cap);
     b.nn = (double *)malloc(sizeof(double) * b.cap);
-    double *sched = (double *)malloc(sizeof(double) * L); /* nnDist_m fed to the schedule */
-    /* k-distances of one length: every DRAG call of that length thresholds them */
+    double *nndist = (double *)malloc(sizeof(double) * L); /* the value each length passes on */
+    /* k-distances of one length: every try at that length thresholds them */
     double *prof = knn > 1 ? (double *)malloc(sizeof(double) * (size_t)(n - minL + 1)) : NULL;
-    if (!b.idx || !b.nn || !sched || (knn > 1 && !prof)) {
-        free(b.idx); free(b.nn); free(sched); free(prof);
+    if (!b.idx || !b.nn || !nndist || (knn > 1 && !prof)) {
+        free(b.idx); free(b.nn); free(nndist); free(prof);
         return -2;
     }
     if (out_heat) memset(out_heat, 0, sizeof(float) * (size_t)L * (size_t)W);
     int rc = 0;
-    for (int32_t m = minL; m <= maxL && !rc; ++m) {
-        const int32_t l = m - minL;
+    for (int32_t l = 0; l < L && !rc; ++l) {
+        const int32_t m = minL + l;
         if (knn > 1) {
             rc = oracle_knn(T, n, m, knn, prof);
             if (rc) break;
@@ -424,54 +448,34 @@ int oracle_merlin_knn(const float *T, int64_t n, int32_t minL, int32_t maxL, int
         }
         int64_t *pidx = out_idx + (int64_t)l * K;
         double *pnn = out_nn + (int64_t)l * K;
-        int calls = 0, ok = 0;
-        double r;
-        if (l == 0) {
-            r = 2.0 * sqrt((double)minL);
-            for (int h = 0;; ++h) {
-                if (h >= 60) r = 0.0;
-                ok = drag_and_pick(T, n, m, r, K, exclusive, &b, pidx, pnn, &rc); ++calls;
-                if (ok || rc || r <= 0.0) break;
-                r = 0.5 * r;
-            }
-        } else if (l <= 4) {
-            r = 0.99 * sched[l - 1];
-            for (int h = 0;; ++h) {
-                if (h >= 3000 || r <= 0.0) r = 0.0;
-                ok = drag_and_pick(T, n, m, r, K, exclusive, &b, pidx, pnn, &rc); ++calls;
-                if (ok || rc || r <= 0.0) break;
-                r = 0.99 * r;
-            }
-        } else {
-            double mean = 0.0, var = 0.0;
-            for (int q = 1; q <= 5; ++q) mean += sched[l - q];
-            mean /= 5.0;
-            for (int q = 1; q <= 5; ++q) var += (sched[l - q] - mean) * (sched[l - q] - mean);
-            double sdv = sqrt(var / 4.0);
-            double step = sdv > 0.0 ? sdv : 0.01 * mean;
-            r = mean - 2.0 * sdv;
-            for (int h = 0;; ++h) {
-                if (h >= 3000 || r <= 0.0) r = 0.0;
-                ok = drag_and_pick(T, n, m, r, K, exclusive, &b, pidx, pnn, &rc); ++calls;
-                if (ok || rc || r <= 0.0) break;
-                r = step > 0.0 ? r - step : 0.0;
-            }
+        const r_rule rule = threshold_rule(l, minL, nndist);
+        double r = rule.first;
+        int tries = 0;
+        for (;;) {
+            if (tries >= rule.max_tries || r <= 0.0) r = 0.0;
+            rc = find_range_discords(T, n, m, r, &b);
+            ++tries;
+            if (rc) break;
+            const int got = oracle_topk(b.idx, b.nn, b.count, m, K, exclusive, pidx, pnn);
+            if (got < 0) { rc = got; break; }
+            if (got == K || r <= 0.0) break;
+            r = rule.minus > 0.0 || rule.scale < 1.0 ? r * rule.scale - rule.minus : 0.0;
         }
         if (rc) break;
-        /* nnDist_m: distance of the K-th pick (or of the last pick when fewer). */
+        /* the K-th pick's distance, or the last pick's when fewer (R6, R8) */
         int got = 0;
         while (got < K && pidx[got] >= 0) ++got;
-        sched[l] = got > 0 ? pnn[got - 1] : 0.0;
+        nndist[l] = got > 0 ? pnn[got - 1] : 0.0;
         if (out_count) out_count[l] = b.count;
         if (out_r) out_r[l] = r;
-        if (out_calls) out_calls[l] = calls;
+        if (out_calls) out_calls[l] = tries;
         if (out_heat) {
             float *row = out_heat + (int64_t)l * W;
             for (int64_t q = 0; q < b.count; ++q)
                 row[b.idx[q]] = (float)(b.nn[q] * b.nn[q] / (2.0 * (double)m));
         }
     }
-    free(b.idx); free(b.nn); free(sched); free(prof);
+    free(b.idx); free(b.nn); free(nndist); free(prof);
     return rc;
 }
 

@@ -585,8 +585,14 @@ palmad_status run_finalize(palmad_ctx* ctx, std::vector<PassLane>& req, const pa
 
 // ====================================================== MERLIN schedule
 
-// The tries of Algorithm 1 for one length (readings R6-R8 of the oracle):
-// the same iterated arithmetic, so the r sequence is bit-identical.
+// The thresholds MERLIN tries for one length (Sec. 2.2): the first length
+// starts at 2 sqrt(minL) and halves; the next four start 1% below the
+// previous length's nnDist and lose 1% per failure; later lengths start at
+// mean - 2 sd of the last five nnDist values and lose sd per failure
+// (0.01 mean when sd is 0).  After 60 halvings, 3000 other failures or at
+// r <= 0 the try runs at r = 0 and is the last one.  Each r is the result of
+// the same FP64 operations in the same order as any other implementation of
+// these rules, so the sequence of r is reproducible bit for bit.
 struct Tries {
     int l = 0;       // length index
     int h = 0;       // try number

@@ -1,6 +1,6 @@
 // Refinement (DRAG phase 2; Algorithm 4, Sec. 3.3), for every lane of a pass.
 //
-//  k_compact      Cand AND Neighbor (Algorithm 4 lines 1-2; already one
+//  k_compact      Cand AND Neighbor (Algorithm 4, its first step; already one
 //                 bitmap here) -> ascending survivor list; one CTA per lane,
 //                 popcount prefix over the bitmap words.
 //  k_plan_count   survivors of this refine round -> pool slots (64-aligned

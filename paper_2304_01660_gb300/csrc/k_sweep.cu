@@ -18,7 +18,7 @@
 //     beyond the FP32 error band) clears the row's and the column's
 //     candidate bit (Cand and Neighbor of Algorithm 3 are one bitmap here,
 //     since refine ANDs them anyway); the warp leaves the strip once every
-//     row is dead (Algorithm 3 lines 14-15) or after `cap` columns;
+//     row is dead (the early exit of Algorithm 3) or after `cap` columns;
 //   * refine sweeps a 1024-column segment of every strip that holds enough
 //     survivors (both sides of the exclusion zone |i - j| < m, which is
 //     masked), starting from directly computed first-column dot products;

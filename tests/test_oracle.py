@@ -11,7 +11,8 @@ factor) fails at least one of them:
   (x vs -x is 2 sqrt(m), x vs a x + b is 0), symmetry and the 2 sqrt(m) bound;
 * nearest neighbour  -- pure-Python brute force on tiny series, exact zero on
   an exactly periodic series, invariance under T -> aT + b, the n = 2m case;
-* DRAG               -- equals {i : MP(i) >= r} with nnDist = MP(i) exactly;
+* range discords     -- the set one DRAG call returns: {i : MP(i) >= r} with
+  nnDist = MP(i), against the C brute force and the pure-Python one;
 * top-K / MERLIN     -- greedy top-K over the brute-force profile, the r
   schedule's closed forms (2 sqrt(minL) / 2^k, 0.99^k, mean - 2 sd - k sd),
   the success condition and the heatmap of Eq. 10.
@@ -199,6 +200,23 @@ def test_drag_equals_thresholded_profile(n, m, seed):
         np.testing.assert_array_equal(idx, want)
         np.testing.assert_allclose(nn, mp[want], rtol=1e-12, atol=1e-12)
         assert np.all(nn >= r)
+
+
+@pytest.mark.parametrize("n,m,seed", [(60, 7, 1), (75, 12, 2)])
+def test_range_discords_match_python_brute_force(n, m, seed):
+    """Sec. 2.1's definition written out in Python: every window whose nearest
+    non-self match is at least r away, with that distance."""
+    T = _rw(n, seed)
+    ref, _ = _py_profile(T, m)
+    fin = np.isfinite(ref)
+    for q in (0.0, 0.3, 0.7, 0.95):
+        r = float(np.quantile(ref[fin], q))
+        idx, nn = oracle.range_discords(T, m, r)
+        want = np.nonzero(fin & (ref >= r))[0]
+        # a window within rounding of r may fall on either side
+        near = np.abs(ref - r) <= 1e-9 * max(1.0, r)
+        assert set(idx.tolist()) ^ set(want.tolist()) <= set(np.nonzero(near)[0].tolist())
+        np.testing.assert_allclose(nn, ref[idx], rtol=1e-9, atol=1e-9)
 
 
 def test_drag_on_sine_finds_injected_anomaly():
