@@ -113,6 +113,10 @@ typedef struct {
                                 fewer than k non-self matches is never a discord.  With
                                 k > 1 no pair prunes (every window is refined over all its
                                 columns), so a call costs a full pass over the pairs. */
+    int32_t no_hints;        /* 0 (default): survivors of candidate select are first tried
+                                against the columns near a pair that pruned the same window
+                                at an earlier length (witness hints; results unchanged);
+                                1: no hints */
 } palmad_options;
 
 /* Per-call counters of the most recent find/drag call. */
@@ -139,6 +143,10 @@ typedef struct {
     double kernel_ms[12];
     int64_t seed_pairs;         /* tensor-core top-row seeds computed (strip x column) */
     double seed_flops;          /* their algorithmic work: 2m per seed */
+    int64_t hint_pairs;         /* pairs evaluated by the witness-hint check */
+    int64_t hint_kills;         /* survivors of select it removed before refine */
+    int64_t refine_strips;      /* strips the recurrence-form refine swept (sum over rounds) */
+    int64_t sweep_survivors;    /* survivors in those strips */
 } palmad_stats;
 
 /* Kernel ids for palmad_stats.launches / kernel_ms. */
@@ -153,7 +161,7 @@ enum {
     PALMAD_K_GATHER = 7,        /* range discords of the call */
     PALMAD_K_TOPK = 8,          /* per-length top-K */
     PALMAD_K_HEAT = 9,          /* heatmap row write (Eq. 10) */
-    PALMAD_K_OTHER = 10,
+    PALMAD_K_HINT = 10,         /* witness-hint check of select survivors */
     PALMAD_K_SEED_TC = 11,      /* tensor-core top-row seeds of the refine sweep */
     PALMAD_K_COUNT = 12
 };

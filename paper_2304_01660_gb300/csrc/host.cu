@@ -51,7 +51,7 @@ struct Small {
     int32_t err;         // a bounded device wait gave up
     int32_t seed_ngroups;
     int32_t pad[5];
-    unsigned long long pairs[8];
+    unsigned long long pairs[12];
 };
 
 struct Timing {
@@ -79,6 +79,7 @@ struct palmad_ctx {
     int sms = 0;
 
     DBuf<float> T;                 // staged series (host entry points)
+    DBuf<int32_t> hints;           // witness hints of the call's series (one int per point)
     std::vector<LaneSet> sets;
     // pass
     DBuf<Lane> lanes;
@@ -264,6 +265,7 @@ palmad_status read_options(palmad_ctx* ctx, const palmad_options* in, palmad_opt
     if (o.refine_seg != 0 && o.refine_seg != kRefineSeg && o.refine_seg != kRefineSegLong)
         return fail(ctx, PALMAD_ERR_ARG, "refine_seg must be 0, 1024 or 2048");
     if (o.knn_k < 0 || o.knn_k > kMaxKnn) return fail(ctx, PALMAD_ERR_ARG, "knn_k must lie in [0, 16]");
+    if (o.no_hints != 0 && o.no_hints != 1) return fail(ctx, PALMAD_ERR_ARG, "no_hints must be 0 or 1");
     return PALMAD_OK;
 }
 
@@ -469,6 +471,16 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     LAUNCH(PALMAD_K_STATS, launch_stats(p, ctx->chain.p, nchains, nmax, ctx->stream));
     if (strips > 0) LAUNCH(PALMAD_K_SELECT, launch_select(p, ctx->sms * 4, ctx->stream));
     LAUNCH(PALMAD_K_COMPACT, launch_compact(p, ctx->stream));
+    {
+        // witness hints: survivors pruned by a pair near where an earlier
+        // length pruned them leave before refine; the survivor list is rebuilt
+        bool hinted = false;
+        for (int l = 0; l < nl; ++l) hinted |= ctx->h_lanes[l].hint != nullptr && ctx->h_lanes[l].prune;
+        if (hinted && hint_supported(p)) {
+            LAUNCH(PALMAD_K_HINT, launch_hint(p, ctx->sms, ctx->stream));
+            LAUNCH(PALMAD_K_COMPACT, launch_compact(p, ctx->stream));
+        }
+    }
     CK(cudaMemcpyAsync(ctx->h_st, ctx->st.p, sizeof(LaneState) * nl, cudaMemcpyDeviceToHost, ctx->stream));
     CKS(sync(ctx));
     for (int l = 0; l < nl; ++l) ctx->stats.survivors += ctx->h_st[l].nsurv;
@@ -536,6 +548,10 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     ctx->stats.select_flops += 5.0 * double(sm.pairs[0]) + 2.0 * mavg * double(sm.pairs[3]);
     ctx->stats.refine_flops += 2.0 * mavg * double(sm.pairs[1]);
     ctx->stats.sweep_flops += 5.0 * double(sm.pairs[4]) + 2.0 * mavg * double(sm.pairs[5]);
+    ctx->stats.refine_strips += int64_t(sm.pairs[9]);
+    ctx->stats.sweep_survivors += int64_t(sm.pairs[10]);
+    ctx->stats.hint_pairs += int64_t(sm.pairs[7]);
+    ctx->stats.hint_kills += int64_t(sm.pairs[8]);
     ctx->stats.seed_pairs += int64_t(sm.pairs[6]);
     ctx->stats.seed_flops += 2.0 * mavg * double(sm.pairs[6]);
     for (int l = 0; l < nl; ++l) {
@@ -646,6 +662,7 @@ struct SeriesJob {
     float* heat = nullptr;      // device heatmap base (row l at heat + l*hw) or nullptr
     int64_t hw = 0;
     int64_t* count_dev = nullptr;  // device [L] counts
+    int32_t* hint = nullptr;       // device [n] witness hints of the series, or nullptr
     int32_t* init_flag = nullptr;  // device int for the non-finite check
     // resumed run: length index minL - minL_sched of the schedule's own run
     // (loff), and the schedule inputs of the lengths before minL (hist)
@@ -698,6 +715,7 @@ Lane make_lane(palmad_ctx* ctx, SeriesJob& s, int32_t li, double r, const palmad
     L.didx = S.didx.p;
     L.dnn = S.dnn.p;
     L.r = r;
+    L.hint = s.hint;
     // k-th neighbour variant: no single pair decides, every window is refined
     L.prune = (r > 0.0 && o.knn_k <= 1) ? 1 : 0;
     L.rho_thr = float(1.0 - r * r / (2.0 * L.m));
@@ -906,6 +924,18 @@ palmad_status run_jobs(palmad_ctx* ctx, std::vector<SeriesJob>& jobs, const palm
         s.first_r.assign(s.loff + s.L, 0.0);
         s.rfin_v.assign(s.loff + s.L, 0.0);
     }
+    // witness hints: one int per point of every series, none recorded yet
+    if (!o.no_hints) {
+        int64_t tot = 0;
+        for (auto& s : jobs) tot += s.n;
+        CKS(ensure(ctx, ctx->hints, size_t(tot)));
+        CK(cudaMemsetAsync(ctx->hints.p, 0xff, sizeof(int32_t) * size_t(tot), ctx->stream));
+        tot = 0;
+        for (auto& s : jobs) {
+            s.hint = ctx->hints.p + tot;
+            tot += s.n;
+        }
+    }
     // initial statistics (Eq. 4 at minL) and the non-finite check
     CKS(ensure(ctx, ctx->init_flags, jobs.size()));
     CK(cudaMemsetAsync(ctx->init_flags.p, 0, sizeof(int32_t) * jobs.size(), ctx->stream));
@@ -1050,6 +1080,7 @@ void palmad_destroy(palmad_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     release(ctx->T);
+    release(ctx->hints);
     for (LaneSet& s : ctx->sets) release_set(s);
     release(ctx->lanes); release(ctx->st); release(ctx->chain); release(ctx->small);
     release(ctx->pidx); release(ctx->pnn);

@@ -131,6 +131,8 @@ __global__ void k_plan_split(const Pass p) {
                            : (p.mixed ? 2 : max(2, (5 * kRefineH + 2 * L.m - 1) / L.m));
         const int sweep = (len >= thr && !(c >> 30)) ? 1 : 0;
         if (sweep) {
+            atomicAdd(p.pairs + 9, 1ull);
+            atomicAdd(p.pairs + 10, static_cast<unsigned long long>(len));
             const int32_t e = atomicAdd(p.nref, 1);
             p.strips[e] = make_int2(l, st);
             if (p.tc_seeds) p.strip_row[e] = len >= p.seed_min ? atomicAdd(&p.st[l].seed_rows, 1) : -1;
@@ -311,7 +313,10 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
                     atomicMax(&p.gmax[g], enc_f32(mx));
                     atomicMax(&p.cmax2[g * p.ncoarse_max + (j0 / p.seg)], enc_f32(mx));  // tile inside one block
                 }
-                if (mx > rho_prune) p.dead[g] = 1;
+                if (mx > rho_prune) {
+                    p.dead[g] = 1;
+                    if (L.hint) L.hint[ci] = int32_t(j0 + kRC / 2);  // witness hint: this tile
+                }
             }
         }
     }

@@ -266,7 +266,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
                     p.cmax[int64_t(g) * p.nchunks_max + chunk] = keep + epsmax;
                     atomicMax(&s_c2[s], enc_f32(keep + epsmax));
                     if (lo > -kInf) atomicMax(&s_lo[s], enc_f32(lo));
-                    if (lo > rp) p.dead[g] = 1;
+                    if (lo > rp) {
+                        p.dead[g] = 1;
+                        if (L.hint) L.hint[__float_as_int(s_rec[s].z) + m - 1] = int32_t(j0) + 32 * wq + 16;  // witness hint
+                    }
                 }
             }
             fence_before();

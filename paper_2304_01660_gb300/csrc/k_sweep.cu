@@ -424,8 +424,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
             }
             if (!REFINE) {
                 // Neighbour (column) marks, row deaths, rows killed elsewhere.
+                // Columns and rows pruned here record where (witness hints for
+                // the next lengths: the strip's middle row, the chunk's middle
+                // column).
                 const uint32_t cw = __reduce_or_sync(kFull, colmask);
-                if (lane == 0 && cw) atomicAnd(&bits[c0 >> 5], ~cw);
+                if (cw) {
+                    uint32_t was = 0;
+                    if (lane == 0) was = atomicAnd(&bits[c0 >> 5], ~cw);
+                    if (Lg.hint) {
+                        was = __shfl_sync(kFull, was, 0);
+                        if (((cw & was) >> lane) & 1u) Lg.hint[c0 + lane] = int32_t(i0 + H / 2);
+                    }
+                }
                 uint32_t newdead = 0;
 #pragma unroll
                 for (int d = 0; d < D; ++d)
@@ -433,6 +443,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
                 if (newdead) {
                     alive &= ~newdead;
                     atomicAnd(&bits[wrd], ~(newdead << sh));
+                    if (Lg.hint)
+#pragma unroll
+                        for (int d = 0; d < D; ++d)
+                            if ((newdead >> d) & 1u) Lg.hint[r0 + d] = int32_t(c0 + 16);
                 }
                 if (r0 < N) alive &= (gbits >> sh) & dmask;
                 if (!__any_sync(kFull, alive)) break;
@@ -448,6 +462,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
                         if (rmax[d] > thr_r[d]) {
                             p.dead[slot[d]] = 1;
                             alive &= ~(1u << d);
+                            if (Lg.hint) Lg.hint[r0 + d] = int32_t(c0 + 16);
                         }
                     }
                     rmax[d] = -kInf;

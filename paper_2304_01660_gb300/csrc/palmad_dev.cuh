@@ -84,6 +84,10 @@ struct Lane {
     int32_t k_lo, k_hi;
     int32_t slot_base;
     int32_t pad;
+    // per window of the series (shared by every lane of the series): a
+    // column near a pair that pruned the window at some length, -1 if none
+    // (nullptr: hints off)
+    int32_t* hint;
 };
 
 // Per-lane device-written state.
@@ -155,8 +159,10 @@ struct Pass {
     int32_t* seed_ngroups;
     int32_t* err;          // set to 1 by a kernel whose bounded wait gave up
     int32_t* work;         // [8] work counters, zeroed per launch group
-    unsigned long long* pairs;  // [8] 0 select, 1 direct refine, 2 fp64, 3 select seeds,
-                                //     4 sweep refine, 5 sweep seeds
+    unsigned long long* pairs;  // [12] 0 select, 1 direct refine, 2 fp64, 3 select seeds,
+                                //      4 sweep refine, 5 sweep seeds, 6 tensor-core seeds,
+                                //      7 hint pairs, 8 survivors removed by hints,
+                                //      9 swept refine strips, 10 survivors in them
     int64_t* pick_idx;     // [nl][K]
     double* pick_nn;       // [nl][K]
 };
@@ -200,6 +206,8 @@ cudaError_t launch_stats_init(const float* T, int64_t n, int32_t m, double* mu, 
 cudaError_t launch_stats(const Pass& p, const int32_t* chain_first, int32_t nchains, int64_t nmax, cudaStream_t s);
 cudaError_t launch_select(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_compact(const Pass& p, cudaStream_t s);
+bool hint_supported(const Pass& p);
+cudaError_t launch_hint(const Pass& p, int sms, cudaStream_t s);
 cudaError_t launch_plan(const Pass& p, cudaStream_t s);
 cudaError_t launch_refine_sweep(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_refine_direct(const Pass& p, int grid, cudaStream_t s);

@@ -21,7 +21,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NONFINITE", -3: "ERR_OOM", -4: "ERR_C
 NOALLOC_MAX_WINDOWS = 1 << 18
 PREC_FP32, PREC_MIXED = 0, 1
 KERNELS = ["stats", "select", "compact", "plan", "refine_sweep", "refine_direct", "recheck", "gather", "topk", "heat",
-           "other", "seed_tc"]
+           "hint", "seed_tc"]
 
 
 class PalmadError(RuntimeError):
@@ -46,6 +46,7 @@ class Options(ctypes.Structure):
         ("seed_rows_max", ctypes.c_int32),
         ("refine_seg", ctypes.c_int32),
         ("knn_k", ctypes.c_int32),
+        ("no_hints", ctypes.c_int32),
     ]
 
 
@@ -69,6 +70,10 @@ class Stats(ctypes.Structure):
         ("kernel_ms", ctypes.c_double * 12),
         ("seed_pairs", ctypes.c_int64),
         ("seed_flops", ctypes.c_double),
+        ("hint_pairs", ctypes.c_int64),
+        ("hint_kills", ctypes.c_int64),
+        ("refine_strips", ctypes.c_int64),
+        ("sweep_survivors", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
