@@ -117,6 +117,23 @@ typedef struct {
                                 against the columns near a pair that pruned the same window
                                 at an earlier length (witness hints; results unchanged);
                                 1: no hints */
+    int32_t spec_scale;      /* batched form: the speculative r of a window of lengths lies
+                                below the schedule's predicted first try by a margin
+                                (2 sd of the last five nnDist, 6% of their mean or 1.5x the
+                                recent shortfall, whichever is largest), and a length whose
+                                schedule needs a lower r is rerun below that r by a similar
+                                margin; this scales both margins in percent (0 = 100).
+                                Smaller margins mean fewer survivors per pass and more
+                                reruns; results are the same for any value */
+    int32_t autotune;        /* 1: palmad_find_discords / _device use the options the
+                                autotuner keeps for this workload bucket (precision,
+                                k, exclusive, and log2 of n, minL, the number of lengths
+                                and topK), tuning on the call's own series first when the
+                                bucket has none (palmad_stats.tune_ms); 0 (default): the
+                                options as given.  Results are the same either way */
+    int32_t refine_rows;     /* rows per strip of the recurrence-form refine: 0 or 128
+                                (default), or 256 (half the top-row dot products per row,
+                                strips live until their last survivor is decided) */
 } palmad_options;
 
 /* Per-call counters of the most recent find/drag call. */
@@ -132,10 +149,11 @@ typedef struct {
     int64_t survivors;          /* candidates handed from select to refine (sum) */
     int64_t discords;           /* range discords at the final r (sum over lengths) */
     double max_fp32_rho_err;    /* max |rho_fast - rho_fp64| seen on re-checked pairs */
-    double select_flops;        /* algorithmic FP32 work of select: 5 per valid pair
-                                   (2 FMA diagonal update + 1 scale) + 2m per top-row seed */
+    double select_flops;        /* algorithmic FP32 work of select: 8 per valid pair (the
+                                   diagonal update of the dot product, its correlation and
+                                   distance, Eq. 6) + 2m per top-row seed */
     double refine_flops;        /* direct-form refine: 2m per evaluated pair */
-    double sweep_flops;         /* recurrence-form refine: 5 per evaluated pair + 2m per
+    double sweep_flops;         /* recurrence-form refine: 8 per evaluated pair + 2m per
                                    direct dot product (top-row and first-column seeds) */
     /* per-kernel launch counts (always) and summed event times in ms
        (profile == 1 only); index = PALMAD_K_* */
@@ -147,7 +165,18 @@ typedef struct {
     int64_t hint_kills;         /* survivors of select it removed before refine */
     int64_t refine_strips;      /* strips the recurrence-form refine swept (sum over rounds) */
     int64_t sweep_survivors;    /* survivors in those strips */
+    double tune_ms;             /* autotuning done by this call (wall ms), 0 if none */
 } palmad_stats;
+
+/* What palmad_autotune timed and chose. */
+typedef struct {
+    int32_t struct_size;        /* sizeof(palmad_tune_report) */
+    int32_t candidates;         /* configurations timed */
+    int32_t block_lo, block_hi; /* first and last length of the timed blocks */
+    double tune_ms;             /* wall time of the whole tuning */
+    double best_ms;             /* summed block time of the chosen configuration */
+    double default_ms;          /* summed block time of the options passed in */
+} palmad_tune_report;
 
 /* Kernel ids for palmad_stats.launches / kernel_ms. */
 enum {
@@ -221,6 +250,17 @@ palmad_status palmad_find_discords_resume(palmad_ctx *ctx, const float *T, int64
                                           int64_t *out_idx, double *out_nndist, int64_t *out_count, double *out_r,
                                           float *out_heatmap);
 
+/*
+ * The values the schedule of Sec. 2.2 carries from each length to the next
+ * (reading R6): per length, the nnDist of its topK-th pick, of its last pick
+ * when fewer, 0 when none.  idx / nndist: [L * topK] results of a find call
+ * (host); out: [L] (host).  A checkpoint at length m0 of a run that started
+ * at minL is out[max(0, l0 - 5) .. l0 - 1], l0 = m0 - minL (the hist of
+ * palmad_find_discords_resume).  No context, no GPU.  Errors: PALMAD_ERR_ARG.
+ */
+palmad_status palmad_schedule_inputs(const int64_t *idx, const double *nndist, int32_t L, int32_t topK,
+                                     double *out);
+
 /* As palmad_find_discords, but T and every output are DEVICE pointers on
  * the context's device; the call is stream-ordered on the context's stream
  * and returns after the results are written. */
@@ -243,6 +283,30 @@ palmad_status palmad_find_discords_batch(palmad_ctx *ctx, int32_t count, const f
                                          double *const *out_r);
 
 /*
+ * Autotuner (no counterpart in the paper, which fixes its launch shapes):
+ * chooses the pass configuration for one series and length range --
+ * lengths per pass (batch_lengths) and the batched form's speculation margin
+ * (spec_scale), the select cap, the refine segment and the refine-form split
+ * (direct_below) and the refine strip height (refine_rows) -- by timing
+ * candidates one setting at a time on blocks of up to 16 lengths at the
+ * start, a third, two thirds and the end of [minL, maxL] of the caller's
+ * series; every block after the first resumes from the schedule inputs of
+ * its preceding lengths, so it meets the thresholds the whole run meets.
+ * Every candidate returns the same results; only the time differs.
+ *   T_dev       [n] float32 device series (the context's device).
+ *   base        options to start from (NULL: defaults); precision, k,
+ *               exclusive_topk and band_rel are kept as given.
+ *   out_opt     receives the chosen options (base with the tuned fields).
+ *   report      NULL or a palmad_tune_report with struct_size set.
+ * The choice is also kept in the context for the workload bucket of
+ * (n, minL, maxL, topK, base) (see palmad_options.autotune).  Synchronous;
+ * takes tens of block runs (seconds on 10^6-point series).
+ */
+palmad_status palmad_autotune(palmad_ctx *ctx, const float *T_dev, int64_t n, int32_t minL, int32_t maxL,
+                              int32_t topK, const palmad_options *base, palmad_options *out_opt,
+                              palmad_tune_report *report);
+
+/*
  * One DRAG call (Algorithm 2; Algorithms 3-4): every range discord of
  * length m at threshold r, in ascending index order.  Host pointers.
  *   T [n] float32, finite; 3 <= m; n >= 2m.
@@ -251,6 +315,43 @@ palmad_status palmad_find_discords_batch(palmad_ctx *ctx, int32_t count, const f
  */
 palmad_status palmad_drag(palmad_ctx *ctx, const float *T, int64_t n, int32_t m, double r, const palmad_options *opt,
                           int64_t *out_idx, double *out_nndist, int64_t cap, int64_t *out_count);
+
+/*
+ * One DRAG call split over ranks (the cluster DRAG of the paper's related
+ * work, Sec. 1): each rank runs one phase on a shard of the pair space and
+ * the ranks exchange one array per phase.
+ *
+ * palmad_drag_select_shard: candidate select (Algorithm 2's first phase;
+ * Algorithm 3) for the rows [row_lo, row_hi) -- every pair (i, j), i in the
+ * rows, j >= i + m, that a select strip scans.  out_bits [(N + 31) / 32]
+ * uint32 (host; bit i of word w is window 32 w + i, N = n - m + 1): set for
+ * the windows no pair of this shard pruned.  The candidates of the whole
+ * call are the bitwise AND of every rank's bitmap (row ranges that cover
+ * [0, N) between them; rounded out to whole 128-row strips).
+ *
+ * palmad_drag_refine_shard: refinement (the second phase; Algorithm 4) of
+ * the candidates cand_bits (host, the ANDed bitmap) against the columns
+ * [col_lo, col_hi) only.  out_nn [N] double (host): -1 for a candidate some
+ * pair of these columns prunes (distance < r), else its FP64
+ * nearest-neighbour distance over the non-self columns of the range (+inf
+ * when there is none), +inf for a window that is no candidate.  With
+ * column ranges that cover [0, N), the elementwise minimum over the ranks
+ * is -1 for every pruned candidate and the exact nearest-neighbour
+ * distance of every other one: the range discords at r are the windows
+ * whose minimum is >= r (every finite one when r <= 0), as palmad_drag
+ * returns them.
+ *
+ * Host pointers; T, m, r as palmad_drag; FP32 forms only (precision MIXED
+ * runs the FP32 direct form here), nearest-neighbour distance only
+ * (knn_k > 1: PALMAD_ERR_UNSUPPORTED).  Errors: PALMAD_ERR_ARG for a bad
+ * range or pointer.
+ */
+palmad_status palmad_drag_select_shard(palmad_ctx *ctx, const float *T, int64_t n, int32_t m, double r,
+                                       int64_t row_lo, int64_t row_hi, const palmad_options *opt,
+                                       uint32_t *out_bits);
+palmad_status palmad_drag_refine_shard(palmad_ctx *ctx, const float *T, int64_t n, int32_t m, double r,
+                                       const uint32_t *cand_bits, int64_t col_lo, int64_t col_hi,
+                                       const palmad_options *opt, double *out_nn);
 
 /*
  * Greedy top-K range discords of a nearest-neighbour profile the caller
@@ -272,6 +373,8 @@ palmad_status palmad_drag(palmad_ctx *ctx, const float *T, int64_t n, int32_t m,
  *   out_nn_dev     [K] double, their distances, 0.0 past the last one (device).
  *   out_count_dev  [1] int64 number of range discords (device) or NULL.
  *   cuda_stream    stream to run on (NULL: the default stream).
+ * The call runs on the calling thread's current CUDA device, which must be
+ * the device holding nn_dev, the outputs and cuda_stream.
  * The call is asynchronous: results are ready once the stream reaches them.
  * Its one intermediate buffer is a fixed device array of the library
  * (PALMAD_NOALLOC_MAX_WINDOWS x 12 bytes per GPU, resident until the process

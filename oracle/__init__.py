@@ -55,6 +55,8 @@ def _load():
             lib.oracle_nn_one.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _f64p, _i64p]
             lib.oracle_range_discords.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _i64p,
                                                   _f64p, ctypes.c_int64, _i64p]
+            lib.oracle_range_discord_windows.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                                         _i64p, ctypes.c_int64, _f64p]
             lib.oracle_topk.argtypes = [_i64p, _f64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
                                         _i64p, _f64p]
             lib.oracle_merlin.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -170,6 +172,19 @@ def range_discords(T, m: int, r: float):
         if cnt.value <= cap:
             return idx[:cnt.value].copy(), nn[:cnt.value].copy()
         cap = cnt.value
+
+
+def range_discord_windows(T, m: int, r: float, windows):
+    """The range-discord test of Sec. 2.1 for the listed windows only: per
+    window its nnDist when it is a range discord at r, NaN otherwise."""
+    T = _f32(T)
+    w = np.ascontiguousarray(windows, dtype=np.int64)
+    out = np.empty(len(w))
+    rc = _load().oracle_range_discord_windows(_p(T, _f32p), len(T), m, float(r), _p(w, _i64p), len(w),
+                                              _p(out, _f64p))
+    if rc:
+        raise ValueError(f"oracle_range_discord_windows rc={rc}")
+    return out
 
 
 # The output of one DRAG call at (m, r): the name the parity tests use.

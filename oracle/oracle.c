@@ -278,6 +278,20 @@ int oracle_drag_knn(const float *T, int64_t n, int32_t m, int32_t k, double r, c
  * *count receives the full number.  Returns 0, or a negative value on bad
  * arguments / allocation failure.
  */
+/* The definition applied to window i: its nnDist when it is a range
+ * discord at r, NAN otherwise. */
+static double range_discord_test(const float *T, int32_t m, int64_t N, int64_t i, double r, const double *mu,
+                                 const double *sd) {
+    double best = INFINITY;
+    for (int64_t j = 0; j < N; ++j) {
+        if (llabs(i - j) < m) continue;
+        double d = sqrt(zdist2(T, m, i, j, mu[i], sd[i], mu[j], sd[j]));
+        if (r > 0.0 && d < r) return NAN;
+        if (d < best) best = d;
+    }
+    return isfinite(best) ? best : NAN;
+}
+
 int oracle_range_discords(const float *T, int64_t n, int32_t m, double r, int64_t *out_idx, double *out_nn,
                           int64_t cap, int64_t *count) {
     if (!T || m < 1 || n < m || !count) return -1;
@@ -287,17 +301,7 @@ int oracle_range_discords(const float *T, int64_t n, int32_t m, double r, int64_
     if (!mu || !sd || !nn) { free(mu); free(sd); free(nn); return -2; }
     oracle_stats(T, n, m, mu, sd);
 #pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t i = 0; i < N; ++i) {
-        double best = INFINITY;
-        int is_discord = 1;
-        for (int64_t j = 0; j < N && is_discord; ++j) {
-            if (llabs(i - j) < m) continue;
-            double d = sqrt(zdist2(T, m, i, j, mu[i], sd[i], mu[j], sd[j]));
-            if (r > 0.0 && d < r) is_discord = 0;
-            else if (d < best) best = d;
-        }
-        nn[i] = (is_discord && isfinite(best)) ? best : NAN;
-    }
+    for (int64_t i = 0; i < N; ++i) nn[i] = range_discord_test(T, m, N, i, r, mu, sd);
     int64_t c = 0;
     for (int64_t i = 0; i < N; ++i) {
         if (isnan(nn[i])) continue;
@@ -309,6 +313,23 @@ int oracle_range_discords(const float *T, int64_t n, int32_t m, double r, int64_
     }
     *count = c;
     free(mu); free(sd); free(nn);
+    return 0;
+}
+
+/* The same test for the listed windows only: out_nn[q] is the nnDist of
+ * window idx[q] when it is a range discord at r, NAN otherwise. */
+int oracle_range_discord_windows(const float *T, int64_t n, int32_t m, double r, const int64_t *idx, int64_t count,
+                                 double *out_nn) {
+    if (!T || m < 1 || n < m || (count > 0 && (!idx || !out_nn))) return -1;
+    int64_t N = n - m + 1;
+    for (int64_t q = 0; q < count; ++q)
+        if (idx[q] < 0 || idx[q] >= N) return -1;
+    double *mu = (double *)malloc(sizeof(double) * N), *sd = (double *)malloc(sizeof(double) * N);
+    if (!mu || !sd) { free(mu); free(sd); return -2; }
+    oracle_stats(T, n, m, mu, sd);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < count; ++q) out_nn[q] = range_discord_test(T, m, N, idx[q], r, mu, sd);
+    free(mu); free(sd);
     return 0;
 }
 

@@ -17,7 +17,11 @@
 //             lower r') only when the schedule needs an r below its r'.
 // Both forms return identical results.
 #include <algorithm>
+#include <array>
+#include <chrono>
 #include <cmath>
+#include <limits>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -31,6 +35,7 @@ using namespace palmad;
 namespace {
 
 constexpr int kDefaultCap = 1024;    // select columns past the strip triangle
+constexpr double kPairFlops = 8.0;   // algorithmic FP32 flops of one recurrence-form pair evaluation
 constexpr int kRefineSeg = 1024;      // refine sweep columns per work item (multiple of 256) ...
 constexpr int kRefineSegLong = 2048;  // ... and for passes with many columns (lanes x N >= kLongPass)
 constexpr int64_t kLongPass = 2000000;
@@ -120,6 +125,8 @@ struct palmad_ctx {
     bool profile = false;
     std::vector<cudaEvent_t> ev_free;
     std::vector<Timing> timings;
+    // autotuner: tuned options per workload bucket (tune_key)
+    std::map<std::array<int64_t, 7>, palmad_options> tuned;
 };
 
 namespace {
@@ -266,6 +273,10 @@ palmad_status read_options(palmad_ctx* ctx, const palmad_options* in, palmad_opt
         return fail(ctx, PALMAD_ERR_ARG, "refine_seg must be 0, 1024 or 2048");
     if (o.knn_k < 0 || o.knn_k > kMaxKnn) return fail(ctx, PALMAD_ERR_ARG, "knn_k must lie in [0, 16]");
     if (o.no_hints != 0 && o.no_hints != 1) return fail(ctx, PALMAD_ERR_ARG, "no_hints must be 0 or 1");
+    if (o.spec_scale < 0 || o.spec_scale > 400) return fail(ctx, PALMAD_ERR_ARG, "spec_scale must lie in [0, 400]");
+    if (o.autotune != 0 && o.autotune != 1) return fail(ctx, PALMAD_ERR_ARG, "autotune must be 0 or 1");
+    if (o.refine_rows != 0 && o.refine_rows != kRefineH && o.refine_rows != kRefineHTall)
+        return fail(ctx, PALMAD_ERR_ARG, "refine_rows must be 0, 128 or 256");
     return PALMAD_OK;
 }
 
@@ -381,8 +392,22 @@ Pass base_pass(palmad_ctx* ctx, int nl, int K, bool exclusive, const palmad_opti
 // One pass over `req` lanes: statistics, select, compaction, refine rounds
 // through the slot pool, gather and top-K.  Fills `out` with every lane's
 // state and top-K picks.
+// A pass either runs whole DRAG calls (kFull) or one phase of a DRAG call
+// whose pair space is split over ranks: kSelect stops after candidate select
+// and copies the lane's bitmap to shard_bits_host; kRefine skips select,
+// takes the candidates from shard_bits_dev and writes every candidate's
+// result over the lane's columns to shard_nn_dev (k_shard_out).
+enum PassMode { kFull = 0, kSelect = 1, kRefine = 2 };
+
+struct ShardIO {
+    PassMode mode = kFull;
+    uint32_t* bits_host = nullptr;      // kSelect: [P] out
+    const uint32_t* bits_dev = nullptr; // kRefine: [P] in (device)
+    double* nn_dev = nullptr;           // kRefine: [N] out (device)
+};
+
 palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool exclusive, const palmad_options& o,
-                       PassOut& out) {
+                       PassOut& out, const ShardIO& io = ShardIO()) {
     const int nl = int(req.size());
     if (nl == 0) return PALMAD_OK;
     if (nl > kMaxLanes) return fail(ctx, PALMAD_ERR_INTERNAL, "too many lanes in a pass");
@@ -393,7 +418,8 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     for (int l = 0; l < nl; ++l) {
         Lane& L = req[l].lane;
         L.kpad = ((L.m + 31) / 32) * 32;
-        L.nstrips = int32_t((L.N + kStripH - 1) / kStripH);
+        L.nstrips = int32_t(std::max<int64_t>(0, std::min<int64_t>((L.N + kStripH - 1) / kStripH, L.strip_lim) -
+                                                  L.strip0));
         L.strip_base = strips;
         strips += L.prune ? L.nstrips : 0;
         if (!L.prune) L.nstrips = 0;
@@ -411,7 +437,10 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     CKS(ensure_pool(ctx, kpad_max, nchunks_max));
     ctx->sets_dirty = true;
     Pass p = base_pass(ctx, nl, K, exclusive, o);
+    if (io.mode == kRefine) strips = 0;
     p.sel_items = strips;
+    p.sharded = io.mode != kFull ? 1 : 0;
+    p.shard_nn = io.nn_dev;
     {
         // a pass with few strips (one lane, a rerun) would leave most warps
         // idle while each runs a long piece: shorter pieces spread its scan
@@ -438,7 +467,11 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     // k-th neighbour re-check needs k columns that reach its threshold, so
     // that variant refines direct strips on the FP32 form, which records
     // the FP32 values themselves.
-    p.mixed = (o.precision == PALMAD_PREC_MIXED && p.knn <= 1 && refine_tc_supported(p)) ? 1 : 0;
+    p.mixed = (o.precision == PALMAD_PREC_MIXED && p.knn <= 1 && !p.sharded && refine_tc_supported(p)) ? 1 : 0;
+    // 256-row refine strips halve the top-row seed work per row: chosen
+    // when asked (the autotuner's refine_rows), never with tensor-core seeds
+    p.refine_h = (o.refine_rows == kRefineHTall && !(o.precision == PALMAD_PREC_MIXED && o.tc_seed_min > 0))
+                     ? kRefineHTall : kRefineH;
     p.direct_below = o.direct_below;
     p.strip_row = ctx->strip_row.p;
     p.seed_ngroups = &ctx->small.p->seed_ngroups;
@@ -470,6 +503,23 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     CK(cudaMemsetAsync(ctx->small.p, 0, sizeof(Small), ctx->stream));
     LAUNCH(PALMAD_K_STATS, launch_stats(p, ctx->chain.p, nchains, nmax, ctx->stream));
     if (strips > 0) LAUNCH(PALMAD_K_SELECT, launch_select(p, ctx->sms * 4, ctx->stream));
+    if (io.mode == kSelect) {
+        const Lane& L0 = ctx->h_lanes[0];
+        CK(cudaMemcpyAsync(io.bits_host, L0.bits, sizeof(uint32_t) * size_t((L0.N + 31) / 32), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CK(cudaMemcpyAsync(ctx->h_small, ctx->small.p, sizeof(Small), cudaMemcpyDeviceToHost, ctx->stream));
+        CKS(sync(ctx));
+        ctx->sets_dirty = false;
+        ctx->stats.select_pairs += int64_t(ctx->h_small->pairs[0]);
+        ctx->stats.device_passes += 1;
+        return PALMAD_OK;
+    }
+    if (io.mode == kRefine) {
+        // the candidates every shard's select left (ANDed by the caller)
+        const Lane& L0 = ctx->h_lanes[0];
+        CK(cudaMemcpyAsync(L0.bits, io.bits_dev, sizeof(uint32_t) * size_t((L0.N + 31) / 32),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     LAUNCH(PALMAD_K_COMPACT, launch_compact(p, ctx->stream));
     {
         // witness hints: survivors pruned by a pair near where an earlier
@@ -520,7 +570,8 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
         if (p.mixed) LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_tc(p, ctx->sms, ctx->stream));
         else LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_direct(p, ctx->sms * 2, ctx->stream));
         LAUNCH(PALMAD_K_RECHECK, launch_recheck(p, ctx->sms * 8, ctx->stream));
-        LAUNCH(PALMAD_K_GATHER, launch_gather(p, ctx->stream));
+        if (io.mode == kRefine) LAUNCH(PALMAD_K_GATHER, launch_shard_out(p, ctx->stream));
+        else LAUNCH(PALMAD_K_GATHER, launch_gather(p, ctx->stream));
         LAUNCH(PALMAD_K_PLAN, launch_round_cleanup(p, ctx->stream));
         bool more = false;
         for (int l = 0; l < nl; ++l) more |= done[l] < ctx->h_st[l].nsurv;
@@ -545,9 +596,12 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     double msum = 0.0;
     for (int l = 0; l < nl; ++l) msum += req[l].lane.m;
     const double mavg = msum / nl;
-    ctx->stats.select_flops += 5.0 * double(sm.pairs[0]) + 2.0 * mavg * double(sm.pairs[3]);
+    // algorithmic work of a pair evaluation: 8 FP32 flops in the recurrence
+    // form (the diagonal update, the correlation and the distance of Eq. 6),
+    // 2m per direct dot product
+    ctx->stats.select_flops += kPairFlops * double(sm.pairs[0]) + 2.0 * mavg * double(sm.pairs[3]);
     ctx->stats.refine_flops += 2.0 * mavg * double(sm.pairs[1]);
-    ctx->stats.sweep_flops += 5.0 * double(sm.pairs[4]) + 2.0 * mavg * double(sm.pairs[5]);
+    ctx->stats.sweep_flops += kPairFlops * double(sm.pairs[4]) + 2.0 * mavg * double(sm.pairs[5]);
     ctx->stats.refine_strips += int64_t(sm.pairs[9]);
     ctx->stats.sweep_survivors += int64_t(sm.pairs[10]);
     ctx->stats.hint_pairs += int64_t(sm.pairs[7]);
@@ -716,6 +770,10 @@ Lane make_lane(palmad_ctx* ctx, SeriesJob& s, int32_t li, double r, const palmad
     L.dnn = S.dnn.p;
     L.r = r;
     L.hint = s.hint;
+    L.strip0 = 0;
+    L.strip_lim = INT64_MAX;
+    L.col_lo = 0;
+    L.col_hi = L.N;
     // k-th neighbour variant: no single pair decides, every window is refined
     L.prune = (r > 0.0 && o.knn_k <= 1) ? 1 : 0;
     L.rho_thr = float(1.0 - r * r / (2.0 * L.m));
@@ -747,13 +805,13 @@ double recent_deficit(const SeriesJob& s, int32_t l0) {
 // Speculative threshold for the window lengths: below the first try of the
 // schedule by about two decrements, 6%, or 1.5x the recent deficit,
 // whichever is largest (never below half the recent mean).
-double speculative_r(const SeriesJob& s, int32_t l0) {  // l0: schedule index
+double speculative_r(const SeriesJob& s, int32_t l0, double scale) {  // l0: schedule index
     double mean = 0.0, var = 0.0;
     for (int q = 1; q <= 5; ++q) mean += s.sched[l0 - q];
     mean /= 5.0;
     for (int q = 1; q <= 5; ++q) var += (s.sched[l0 - q] - mean) * (s.sched[l0 - q] - mean);
     const double sdv = std::sqrt(var / 4.0);
-    const double margin = std::max({2.0 * sdv, 0.06 * mean, 1.5 * recent_deficit(s, l0)});
+    const double margin = scale * std::max({2.0 * sdv, 0.06 * mean, 1.5 * recent_deficit(s, l0)});
     return std::max(mean - 2.0 * sdv - margin, 0.5 * mean);
 }
 
@@ -799,7 +857,7 @@ void series_request(palmad_ctx* ctx, SeriesJob& s, std::vector<PassLane>& req, s
     if (s.W > 1 && s.l + s.loff >= 5) {
         s.wl0 = s.l;
         s.wn = std::min<int32_t>(s.W, s.L - s.l);
-        s.rspec.assign(s.wn, speculative_r(s, s.l + s.loff));
+        s.rspec.assign(s.wn, speculative_r(s, s.l + s.loff, o.spec_scale > 0 ? 0.01 * o.spec_scale : 1.0));
         for (int w = 0; w < s.wn; ++w) push(s.wl0 + w, s.rspec[w], w + 1 < s.wn);
         s.phase = SeriesJob::kWindow;
         return;
@@ -831,7 +889,8 @@ void series_replay(palmad_ctx* ctx, SeriesJob& s, std::vector<PassLane>& fin, co
                 // the schedule needs r below this length's r': rerun it lower,
                 // by at least three decrements, 10% or 1.5x the recent deficit
                 const double step = s.tr.step > 0.0 ? s.tr.step : 0.01 * r;
-                const double drop = std::max({3.0 * step, 0.1 * r, 1.5 * recent_deficit(s, s.l + s.loff)});
+                const double drop = (o.spec_scale > 0 ? 0.01 * o.spec_scale : 1.0) *
+                                    std::max({3.0 * step, 0.1 * r, 1.5 * recent_deficit(s, s.l + s.loff)});
                 s.rerun_l = s.l;
                 s.rerun_r = r - drop;
                 if (s.rerun_r < 0.05 * r) s.rerun_r = 0.05 * r;  // stay clear of the r = 0 full profile
@@ -1025,6 +1084,219 @@ void count_discords(palmad_ctx* ctx, const std::vector<int64_t>& counts) {
     for (int64_t c : counts) ctx->stats.discords += c;
 }
 
+// ============================================================= autotuner
+//
+// The pass configuration -- lengths per pass and the speculation margin of
+// the batched form, the select cap, the refine segment and the split
+// between the refine forms -- changes how fast a call runs, never what it
+// returns.  Which configuration is fastest depends on the data: on short
+// series many lengths per pass amortise launches, on long quasi-periodic
+// series every speculative margin multiplies the survivors refine must
+// scan.  The tuner times candidates on a block of lengths of the caller's
+// own series (a fresh schedule started mid-range) by coordinate descent
+// and keeps the fastest per workload bucket.
+
+std::array<int64_t, 7> tune_key(int64_t n, int32_t minL, int32_t maxL, int32_t topK, const palmad_options& o) {
+    auto lg = [](int64_t v) { int64_t b = 0; while (v > 1) { v >>= 1; ++b; } return b; };
+    return {int64_t(o.precision), int64_t(o.knn_k > 1 ? o.knn_k : 1), lg(n), lg(minL), lg(maxL - minL + 1),
+            lg(topK), int64_t(o.exclusive_topk != 0)};
+}
+
+// A block of lengths [lo, hi] of MERLIN over a device series, resumed from
+// the schedule inputs of the lengths before it (hist, lengths since the
+// run's first length minL_sched) exactly as the whole run reaches it.
+struct Block {
+    int32_t lo = 0, hi = 0, minL_sched = 0;
+    std::vector<double> hist;
+};
+
+// Wall time of one block; sched_out (optional) receives the schedule input
+// of every length of the block.
+palmad_status time_block(palmad_ctx* ctx, const float* T_dev, int64_t n, const Block& b, int32_t K,
+                         const palmad_options& o, double* ms, std::vector<double>* sched_out = nullptr) {
+    std::vector<SeriesJob> jobs(1);
+    SeriesJob& s = jobs[0];
+    s.T = T_dev;
+    s.n = n;
+    s.minL = b.lo;
+    s.maxL = b.hi;
+    s.K = K;
+    s.exclusive = o.exclusive_topk != 0;
+    s.W = std::max(1, o.batch_lengths);
+    s.minL_sched = b.minL_sched;
+    s.loff = b.lo - b.minL_sched;
+    s.hist = b.hist;
+    DBuf<int64_t> cnt;
+    CKS(ensure(ctx, cnt, size_t(b.hi - b.lo + 1)));
+    s.count_dev = cnt.p;
+    CK(cudaStreamSynchronize(ctx->stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    palmad_status st = run_jobs(ctx, jobs, o);
+    if (st == PALMAD_OK) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = fail(ctx, PALMAD_ERR_CUDA, std::string("tuning run: ") + cudaGetErrorString(e));
+    }
+    *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    tcollect(ctx);
+    release(cnt);
+    if (st == PALMAD_OK && sched_out) {
+        sched_out->clear();
+        for (int32_t l = 0; l <= b.hi - b.lo; ++l) sched_out->push_back(s.sched[s.loff + l]);
+    }
+    return st;
+}
+
+palmad_status tune(palmad_ctx* ctx, const float* T_dev, int64_t n, int32_t minL, int32_t maxL, int32_t topK,
+                   const palmad_options& base, palmad_options* out, palmad_tune_report* rep) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int32_t L = maxL - minL + 1;
+    palmad_options cur = base;
+    cur.autotune = 0;
+    cur.profile = 0;
+    // Blocks of up to 16 lengths at the start, a third, two thirds and the
+    // end of the range.  Each later block resumes from the schedule inputs
+    // of its five preceding lengths, found by a short untimed run started at
+    // the first of them: a length's picks (and so its schedule input) do not
+    // depend on the thresholds tried, so the block then follows the very
+    // thresholds the whole run meets there.
+    const int32_t B = std::min<int32_t>(L, 16);
+    std::vector<Block> blocks;
+    for (int q = 0; q < 4; ++q) {
+        const int32_t lo = minL + int32_t(int64_t(L - B) * q / 3);
+        if (!blocks.empty() && lo <= blocks.back().hi) continue;
+        Block b;
+        b.lo = lo;
+        b.hi = lo + B - 1;
+        b.minL_sched = minL;
+        if (lo > minL) {
+            Block pre;
+            pre.lo = std::max(minL, lo - 5);
+            pre.hi = lo - 1;
+            pre.minL_sched = pre.lo;
+            palmad_options po = cur;
+            po.batch_lengths = 1;
+            double t = 0.0;
+            CKS(time_block(ctx, T_dev, n, pre, topK, po, &t, &b.hist));
+            b.minL_sched = pre.lo;
+        }
+        blocks.push_back(b);
+    }
+    int evals = 0;
+    // the summed block time, the best of up to three runs when short
+    auto measure = [&](const palmad_options& o, double* ms) -> palmad_status {
+        double best = 1e300;
+        for (int k = 0; k < 3; ++k) {
+            double tot = 0.0;
+            for (const Block& b : blocks) {
+                double t = 0.0;
+                CKS(time_block(ctx, T_dev, n, b, topK, o, &t));
+                tot += t;
+            }
+            best = std::min(best, tot);
+            if (tot > 50.0) break;
+        }
+        ++evals;
+        *ms = best;
+        return PALMAD_OK;
+    };
+    double warm = 0.0;
+    CKS(time_block(ctx, T_dev, n, blocks[0], topK, cur, &warm));  // first use allocates the buffers
+    double best_ms = 0.0;
+    CKS(measure(cur, &best_ms));
+    const double default_ms = best_ms;
+    auto consider = [&](palmad_options o) -> palmad_status {
+        double t = 0.0;
+        CKS(measure(o, &t));
+        if (t < best_ms) {
+            best_ms = t;
+            cur = o;
+        }
+        return PALMAD_OK;
+    };
+    // lengths per pass and the speculation margin
+    {
+        const palmad_options start = cur;
+        for (int32_t W : {1, 2, 4, 16})
+            for (int32_t sc : {100, 40}) {
+                if (W == 1 && sc != 100) continue;
+                palmad_options o = start;
+                o.batch_lengths = W;
+                o.spec_scale = sc;
+                if (o.batch_lengths == std::max(1, start.batch_lengths) && o.spec_scale == (start.spec_scale ? start.spec_scale : 100)) continue;
+                CKS(consider(o));
+            }
+    }
+    // select cap
+    {
+        const palmad_options start = cur;
+        for (int32_t cap : {512, 2048}) {
+            palmad_options o = start;
+            o.select_cap = cap;
+            CKS(consider(o));
+        }
+    }
+    // refine segment
+    {
+        const palmad_options start = cur;
+        for (int32_t seg : {1024, 2048}) {
+            palmad_options o = start;
+            o.refine_seg = seg;
+            CKS(consider(o));
+        }
+    }
+    // rows per refine strip
+    {
+        const palmad_options start = cur;
+        palmad_options o = start;
+        o.refine_rows = kRefineHTall;
+        CKS(consider(o));
+    }
+    // strips below this many survivors take the direct form
+    {
+        const palmad_options start = cur;
+        for (int32_t db : {2, 4, 8}) {
+            palmad_options o = start;
+            o.direct_below = db;
+            CKS(consider(o));
+        }
+    }
+    cur.profile = base.profile;
+    cur.autotune = base.autotune;
+    *out = cur;
+    ctx->tuned[tune_key(n, minL, maxL, topK, base)] = cur;
+    if (rep) {
+        rep->candidates = evals;
+        rep->block_lo = blocks.front().lo;
+        rep->block_hi = blocks.back().hi;
+        rep->best_ms = best_ms;
+        rep->default_ms = default_ms;
+        rep->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return PALMAD_OK;
+}
+
+// Options of a find call with autotune set: the bucket's tuned options,
+// tuning on the call's own series first when the bucket has none.
+palmad_status tuned_options(palmad_ctx* ctx, const float* T_dev, int64_t n, int32_t minL, int32_t maxL, int32_t topK,
+                            palmad_options& o) {
+    if (!o.autotune) return PALMAD_OK;
+    auto it = ctx->tuned.find(tune_key(n, minL, maxL, topK, o));
+    if (it != ctx->tuned.end()) {
+        const int32_t prof = o.profile;
+        o = it->second;
+        o.profile = prof;
+        return PALMAD_OK;
+    }
+    palmad_tune_report rep{};
+    palmad_options t{};
+    CKS(tune(ctx, T_dev, n, minL, maxL, topK, o, &t, &rep));
+    t.profile = o.profile;
+    o = t;
+    reset_stats(ctx);
+    ctx->stats.tune_ms = rep.tune_ms;
+    return PALMAD_OK;
+}
+
 }  // namespace
 
 // ======================================================================= C ABI
@@ -1127,6 +1399,7 @@ palmad_status palmad_find_discords_device(palmad_ctx* ctx, const float* T_dev, i
     std::vector<SeriesJob> jobs(1);
     SeriesJob& s = jobs[0];
     CKS(aligned_series(ctx, T_dev, n, ctx->T, &s.T));
+    CKS(tuned_options(ctx, s.T, n, minL, maxL, topK, o));
     s.n = n;
     s.minL = minL;
     s.maxL = maxL;
@@ -1177,6 +1450,7 @@ static palmad_status find_one(palmad_ctx* ctx, const float* T, int64_t n, int32_
     const int64_t hw = n - minL + 1;
     CKS(ensure(ctx, ctx->T, size_t(n)));
     CK(cudaMemcpyAsync(ctx->T.p, T, size_t(n) * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    if (minL_sched == minL) CKS(tuned_options(ctx, ctx->T.p, n, minL, maxL, topK, o));
     DBuf<int64_t> cnt;
     DBuf<float> heat;
     CKS(ensure(ctx, cnt, L));
@@ -1317,18 +1591,49 @@ palmad_status palmad_find_discords_batch(palmad_ctx* ctx, int32_t count, const f
     return st;
 }
 
-palmad_status palmad_drag(palmad_ctx* ctx, const float* T, int64_t n, int32_t m, double r, const palmad_options* opt,
-                          int64_t* out_idx, double* out_nndist, int64_t cap, int64_t* out_count) {
-    if (!ctx) return PALMAD_ERR_ARG;
-    if (m < 3) return fail(ctx, PALMAD_ERR_ARG, "m must be >= 3");
-    if (n < 2 * int64_t(m)) return fail(ctx, PALMAD_ERR_ARG, "n must be >= 2*m");
-    if (n > (int64_t(1) << 30)) return fail(ctx, PALMAD_ERR_UNSUPPORTED, "n above 2^30 is not supported");
-    if (!T || !out_count || cap < 0 || (cap > 0 && (!out_idx || !out_nndist)))
-        return fail(ctx, PALMAD_ERR_ARG, "bad pointer or cap");
-    if (!std::isfinite(r)) return fail(ctx, PALMAD_ERR_ARG, "r must be finite");
+palmad_status palmad_schedule_inputs(const int64_t* idx, const double* nndist, int32_t L, int32_t topK,
+                                     double* out) {
+    if (L < 0 || topK < 1 || (L > 0 && (!idx || !nndist || !out))) return PALMAD_ERR_ARG;
+    for (int32_t l = 0; l < L; ++l) {
+        int32_t got = 0;
+        while (got < topK && idx[int64_t(l) * topK + got] >= 0) ++got;
+        out[l] = got > 0 ? nndist[int64_t(l) * topK + got - 1] : 0.0;
+    }
+    return PALMAD_OK;
+}
+
+palmad_status palmad_autotune(palmad_ctx* ctx, const float* T_dev, int64_t n, int32_t minL, int32_t maxL,
+                              int32_t topK, const palmad_options* base, palmad_options* out_opt,
+                              palmad_tune_report* report) {
+    CKS(check_args(ctx, n, minL, maxL, topK));
+    if (!T_dev || !out_opt) return fail(ctx, PALMAD_ERR_ARG, "null T or output pointer");
+    if (report && report->struct_size != int32_t(sizeof(palmad_tune_report)))
+        return fail(ctx, PALMAD_ERR_ARG, "palmad_tune_report.struct_size mismatch");
     palmad_options o;
-    CKS(read_options(ctx, opt, o));
+    CKS(read_options(ctx, base, o));
     CKS(begin_call(ctx, o));
+    const float* T;
+    CKS(aligned_series(ctx, T_dev, n, ctx->T, &T));
+    palmad_tune_report rep{};
+    rep.struct_size = sizeof(palmad_tune_report);
+    palmad_options t{};
+    CKS(tune(ctx, T, n, minL, maxL, topK, o, &t, &rep));
+    reset_stats(ctx);
+    ctx->stats.tune_ms = rep.tune_ms;
+    *out_opt = t;
+    if (report) *report = rep;
+    return PALMAD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One lane for a single DRAG call at (m, r) over a host series: uploads T,
+// computes the statistics of length m and checks T; the lane covers the
+// whole pair space.
+palmad_status drag_lane(palmad_ctx* ctx, const float* T, int64_t n, int32_t m, double r, const palmad_options& o,
+                        std::vector<PassLane>& req) {
     CKS(ensure(ctx, ctx->T, size_t(n)));
     CK(cudaMemcpyAsync(ctx->T.p, T, size_t(n) * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     if (ctx->sets.empty()) ctx->sets.resize(1);
@@ -1342,7 +1647,7 @@ palmad_status palmad_drag(palmad_ctx* ctx, const float* T, int64_t n, int32_t m,
     CK(cudaMemcpyAsync(&flag, ctx->init_flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
     CKS(sync(ctx));
     if (flag & 1) return fail(ctx, PALMAD_ERR_NONFINITE, "T holds a NaN or an infinity");
-    std::vector<PassLane> req(1);
+    req.assign(1, PassLane{});
     Lane& L = req[0].lane;
     L = Lane{};
     L.T = ctx->T.p;
@@ -1358,7 +1663,39 @@ palmad_status palmad_drag(palmad_ctx* ctx, const float* T, int64_t n, int32_t m,
     L.prune = (r > 0.0 && o.knn_k <= 1) ? 1 : 0;
     L.rho_thr = float(1.0 - r * r / (2.0 * m));
     L.band = float(o.band_rel * r * r / m);
+    L.strip0 = 0;
+    L.strip_lim = INT64_MAX;
+    L.col_lo = 0;
+    L.col_hi = N;
     req[0].state = LaneState{};
+    return PALMAD_OK;
+}
+
+palmad_status check_drag_args(palmad_ctx* ctx, const float* T, int64_t n, int32_t m, double r) {
+    if (!ctx) return PALMAD_ERR_ARG;
+    if (m < 3) return fail(ctx, PALMAD_ERR_ARG, "m must be >= 3");
+    if (n < 2 * int64_t(m)) return fail(ctx, PALMAD_ERR_ARG, "n must be >= 2*m");
+    if (n > (int64_t(1) << 30)) return fail(ctx, PALMAD_ERR_UNSUPPORTED, "n above 2^30 is not supported");
+    if (!T) return fail(ctx, PALMAD_ERR_ARG, "null T");
+    if (!std::isfinite(r)) return fail(ctx, PALMAD_ERR_ARG, "r must be finite");
+    return PALMAD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+palmad_status palmad_drag(palmad_ctx* ctx, const float* T, int64_t n, int32_t m, double r, const palmad_options* opt,
+                          int64_t* out_idx, double* out_nndist, int64_t cap, int64_t* out_count) {
+    CKS(check_drag_args(ctx, T, n, m, r));
+    if (!out_count || cap < 0 || (cap > 0 && (!out_idx || !out_nndist)))
+        return fail(ctx, PALMAD_ERR_ARG, "bad pointer or cap");
+    palmad_options o;
+    CKS(read_options(ctx, opt, o));
+    CKS(begin_call(ctx, o));
+    std::vector<PassLane> req;
+    CKS(drag_lane(ctx, T, n, m, r, o, req));
+    LaneSet& S = ctx->sets[0];
     PassOut out;
     CKS(run_pass(ctx, req, 1, true, o, out));
     const int64_t cnt = out.st[0].dcount;
@@ -1375,6 +1712,83 @@ palmad_status palmad_drag(palmad_ctx* ctx, const float* T, int64_t n, int32_t m,
     }
     *out_count = cnt;
     return PALMAD_OK;
+}
+
+palmad_status palmad_drag_select_shard(palmad_ctx* ctx, const float* T, int64_t n, int32_t m, double r,
+                                       int64_t row_lo, int64_t row_hi, const palmad_options* opt, uint32_t* out_bits) {
+    CKS(check_drag_args(ctx, T, n, m, r));
+    const int64_t N = n - m + 1;
+    if (!out_bits) return fail(ctx, PALMAD_ERR_ARG, "null out_bits");
+    if (row_lo < 0 || row_hi < row_lo || row_hi > N) return fail(ctx, PALMAD_ERR_ARG, "need 0 <= row_lo <= row_hi <= N");
+    palmad_options o;
+    CKS(read_options(ctx, opt, o));
+    if (o.knn_k > 1) return fail(ctx, PALMAD_ERR_UNSUPPORTED, "shards run the nearest-neighbour distance only");
+    CKS(begin_call(ctx, o));
+    std::vector<PassLane> req;
+    CKS(drag_lane(ctx, T, n, m, r, o, req));
+    Lane& L = req[0].lane;
+    L.strip0 = row_lo / kStripH;
+    L.strip_lim = (row_hi + kStripH - 1) / kStripH;
+    if (row_hi == row_lo) L.strip_lim = L.strip0;
+    PassOut out;
+    ShardIO io;
+    io.mode = kSelect;
+    io.bits_host = out_bits;
+    CKS(run_pass(ctx, req, 1, true, o, out, io));
+    ctx->stats.drag_calls = 1;
+    ctx->stats.lengths = 1;
+    return PALMAD_OK;
+}
+
+palmad_status palmad_drag_refine_shard(palmad_ctx* ctx, const float* T, int64_t n, int32_t m, double r,
+                                       const uint32_t* cand_bits, int64_t col_lo, int64_t col_hi,
+                                       const palmad_options* opt, double* out_nn) {
+    CKS(check_drag_args(ctx, T, n, m, r));
+    const int64_t N = n - m + 1;
+    if (!cand_bits || !out_nn) return fail(ctx, PALMAD_ERR_ARG, "null cand_bits or out_nn");
+    if (col_lo < 0 || col_hi < col_lo || col_hi > N) return fail(ctx, PALMAD_ERR_ARG, "need 0 <= col_lo <= col_hi <= N");
+    palmad_options o;
+    CKS(read_options(ctx, opt, o));
+    if (o.knn_k > 1) return fail(ctx, PALMAD_ERR_UNSUPPORTED, "shards run the nearest-neighbour distance only");
+    CKS(begin_call(ctx, o));
+    std::vector<PassLane> req;
+    CKS(drag_lane(ctx, T, n, m, r, o, req));
+    Lane& L = req[0].lane;
+    L.col_lo = col_lo;
+    L.col_hi = col_hi;
+    const int64_t P = (N + 31) / 32;
+    DBuf<uint32_t> bits;
+    DBuf<double> nn;
+    palmad_status st = ensure(ctx, bits, size_t(P));
+    if (st == PALMAD_OK) st = ensure(ctx, nn, size_t(N));
+    cudaError_t e = cudaSuccess;
+    if (st == PALMAD_OK) e = cudaMemcpyAsync(bits.p, cand_bits, sizeof(uint32_t) * size_t(P), cudaMemcpyHostToDevice,
+                                             ctx->stream);
+    // +inf for every window: windows that are no candidate keep it
+    if (st == PALMAD_OK && e == cudaSuccess) {
+        std::vector<double> inf(size_t(N), std::numeric_limits<double>::infinity());
+        e = cudaMemcpyAsync(nn.p, inf.data(), sizeof(double) * size_t(N), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    }
+    if (st == PALMAD_OK && e != cudaSuccess) st = fail(ctx, PALMAD_ERR_CUDA, cudaGetErrorString(e));
+    if (st == PALMAD_OK) {
+        PassOut out;
+        ShardIO io;
+        io.mode = kRefine;
+        io.bits_dev = bits.p;
+        io.nn_dev = nn.p;
+        st = run_pass(ctx, req, 1, true, o, out, io);
+    }
+    if (st == PALMAD_OK) {
+        e = cudaMemcpyAsync(out_nn, nn.p, sizeof(double) * size_t(N), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = fail(ctx, PALMAD_ERR_CUDA, cudaGetErrorString(e));
+        ctx->stats.drag_calls = 1;
+        ctx->stats.lengths = 1;
+    }
+    release(bits);
+    release(nn);
+    return st;
 }
 
 }  // extern "C"

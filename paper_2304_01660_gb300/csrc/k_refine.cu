@@ -104,7 +104,7 @@ __global__ void k_plan_count(const Pass p) {
         const int32_t w = L.surv[k];
         p.slot_win[g] = w;
         L.slot_of[w] = g;
-        const int32_t st = w / kRefineH;
+        const int32_t st = w / p.refine_h;
         atomicAdd(&L.scount[st], 1);                              // survivors of the strip
         if (L.win[w].z == 0.f) atomicOr(&L.scount[st], 1 << 30);  // a flat window among them
     }
@@ -117,8 +117,8 @@ __global__ void k_plan_split(const Pass p) {
         const int l = p.slot_lane[g];
         const Lane& L = p.lanes[l];
         const int32_t k = L.k_lo + (g - L.slot_base);
-        const int32_t st = w / kRefineH;
-        if (k > L.k_lo && L.surv[k - 1] / kRefineH == st) continue;  // not the first of its strip
+        const int32_t st = w / p.refine_h;
+        if (k > L.k_lo && L.surv[k - 1] / p.refine_h == st) continue;  // not the first of its strip
         const int32_t c = L.scount[st];
         const int32_t len = c & ((1 << 30) - 1);
         // sweep when cheaper than the direct form: FP32 direct costs 2m flops per
@@ -128,7 +128,7 @@ __global__ void k_plan_split(const Pass p) {
         // slower than the sweep, whose strips stop at the first 32-column
         // chunk where every row is pruned
         const int32_t thr = p.direct_below > 0 ? p.direct_below
-                           : (p.mixed ? 2 : max(2, (5 * kRefineH + 2 * L.m - 1) / L.m));
+                           : (p.mixed ? 2 : max(2, (5 * p.refine_h + 2 * L.m - 1) / L.m));
         const int sweep = (len >= thr && !(c >> 30)) ? 1 : 0;
         if (sweep) {
             atomicAdd(p.pairs + 9, 1ull);
@@ -177,7 +177,7 @@ __global__ void k_prep(const Pass p) {
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
         if (lane == 0) p.asum[g] = part;
-        if (p.route[g] == 1)  // the direct forms raise these with atomicMax; enc_f32 order: 0 is lowest
+        if (p.route[g] == 1 || p.sharded)  // raised with atomicMax / written per segment; enc_f32 order: 0 is lowest
             for (int k = lane; k < p.ncoarse_max; k += 32) p.cmax2[g * p.ncoarse_max + k] = 0u;
     }
 }
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
         const int64_t j0 = int64_t(t) * kRC;
         // entries [gbase, gbase+64) of the lane's packed direct list
         const int32_t nd = p.st[l].ndirect - int32_t(gbase - L.slot_base);
-        if (tid < kRS && tid < nd && j0 < N) {
+        if (tid < kRS && tid < nd && j0 < N && j0 < L.col_hi && j0 + kRC > L.col_lo) {
             if (!__ldcg(&p.dead[p.dlist[gbase + tid]])) atomicOr(&alive_s, 1);
         }
         __syncthreads();
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int64_t j = jc + c;
-            colok[c] = j < N;
+            colok[c] = j < N && j >= L.col_lo && j < L.col_hi;
             const float4 r = colok[c] ? win[j] : make_float4(0.f, 0.f, 0.f, 0.f);
             invj[c] = r.z;
             muj[c] = r.w;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kRecheckWarps * 32) k_recheck(const Pass p) {
                     // FP32 rho of the chunk's columns, one per lane
                     const int64_t j = int64_t(qq) * 32 + lane;
                     float rho32 = -kInf;
-                    const bool valid = j < N && (j - c >= m || c - j >= m);
+                    const bool valid = j < N && (j - c >= m || c - j >= m) && j >= L.col_lo && j < L.col_hi;
                     if (valid) {
                         const float4 rj = win[j];
                         float acc = 0.f;

@@ -108,7 +108,7 @@ __global__ void k_seed_prep(const Pass p) {
         if (loc < 0 || loc >= S.seed_eff) continue;
         const Lane& L = p.lanes[sl.x];
         const int64_t row = int64_t(S.seed_base) + loc;
-        const int64_t i0 = int64_t(sl.y) * kRefineH;
+        const int64_t i0 = int64_t(sl.y) * p.refine_h;
         const float mu = L.win[i0].w;
         float part = 0.f;
         float* dst = p.topcen + row * p.kpad_max;

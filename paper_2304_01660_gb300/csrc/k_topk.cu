@@ -31,7 +31,21 @@ __global__ void k_round_cleanup(const Pass p) {
         const int32_t w = p.slot_win[g];
         if (w < 0) continue;
         L.slot_of[w] = -1;
-        L.scount[w / kRefineH] = 0;
+        L.scount[w / p.refine_h] = 0;
+    }
+}
+
+// Result of a refine shard for the round's candidates: -1 for a candidate
+// that some pair of the shard's columns pruned (d < r), else its FP64
+// nearest-neighbour distance over those columns (+inf when none is a
+// non-self match).  One lane per pass.
+__global__ void k_shard_out(const Pass p) {
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < p.nslots; g += gridDim.x * blockDim.x) {
+        const int32_t w = p.slot_win[g];
+        if (w < 0) continue;
+        const unsigned long long b = p.nn2[g];
+        p.shard_nn[w] = p.dead[g] ? -1.0 : (b >= kInfBits ? __longlong_as_double(static_cast<long long>(kInfBits))
+                                                          : sqrt(__longlong_as_double(static_cast<long long>(b))));
     }
 }
 
@@ -180,6 +194,12 @@ cudaError_t launch_round_cleanup(const Pass& p, cudaStream_t s) {
     if (p.nslots <= 0) return cudaSuccess;
     const int grid = int(min64((int64_t(p.nslots) + 255) / 256, 1024));
     k_round_cleanup<<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_out(const Pass& p, cudaStream_t s) {
+    if (p.nslots <= 0) return cudaSuccess;
+    k_shard_out<<<int(min64((int64_t(p.nslots) + 255) / 256, 1024)), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -21,7 +21,8 @@ namespace palmad {
 constexpr int kWarp = 32;
 constexpr float kInf = __builtin_huge_valf();
 constexpr int kStripH = 128;   // rows per strip of the select sweep (32 lanes x 4)
-constexpr int kRefineH = 128;  // rows per strip of the refine sweep (32 lanes x 4)
+constexpr int kRefineH = 128;  // rows per strip of the refine sweep (32 lanes x 4) ...
+constexpr int kRefineHTall = 256;  // ... or, chosen per pass, 32 lanes x 8 (fewer top-row seeds per row)
 constexpr int kCoarseMin = 1024;  // smallest coarse block of the chunk maxima (the pool is sized for it)
 constexpr int kSelPieceCols = 512;       // columns per select work item (a strip's scan is cut into pieces)
 constexpr int kSelPieceColsShort = 256;  // the same for passes with too few strips to fill the GPU
@@ -88,6 +89,12 @@ struct Lane {
     // column near a pair that pruned the window at some length, -1 if none
     // (nullptr: hints off)
     int32_t* hint;
+    // a shard of the pair space (one series split over ranks): select runs
+    // the strips from strip0 on (nstrips of them), refine compares
+    // survivors with the columns [col_lo, col_hi) only; whole lane
+    // otherwise (strip0 = 0, col_lo = 0, col_hi >= N)
+    int64_t strip0, strip_lim;  // select strips [strip0, min(all strips, strip_lim))
+    int64_t col_lo, col_hi;
 };
 
 // Per-lane device-written state.
@@ -127,7 +134,7 @@ struct Pass {
     int32_t nchunks_max;   // 32-column chunks of the largest lane
     int32_t mixed;         // 1: direct refine on the tensor cores (k_refine_tc)
     int32_t kpad_pass;     // largest kpad of this pass's lanes (kpad_max is the pool's stride)
-    int32_t pad5;
+    int32_t refine_h;      // rows per refine strip this pass: kRefineH or kRefineHTall
     int32_t* slot_lane;    // [slots] lane of each slot
     int32_t* slot_win;     // [slots] window of each slot, -1 for padding
     int32_t* route;        // [slots] 0 sweep, 1 direct, -1 none
@@ -157,6 +164,9 @@ struct Pass {
     int32_t pad4;
     int4* seed_groups;     // (lane, first row, rows, -) per group of <= 32 rows of one lane
     int32_t* seed_ngroups;
+    int32_t sharded;       // 1: a lane restricts its columns (k_prep clears every coarse maximum)
+    int32_t pad7;
+    double* shard_nn;      // [N of lane 0] per-candidate result of a refine shard, or nullptr
     int32_t* err;          // set to 1 by a kernel whose bounded wait gave up
     int32_t* work;         // [8] work counters, zeroed per launch group
     unsigned long long* pairs;  // [12] 0 select, 1 direct refine, 2 fp64, 3 select seeds,
@@ -171,7 +181,7 @@ struct Pass {
 // per-length window maxima the statistics kernel records:
 //   a = |df_i| inv_i,  b = |dg_i| inv_i.
 // A row of a strip sweep is at most H-1 recurrence steps away from a
-// directly computed dot product; each step adds at most
+// directly computed dot product (H the tallest strip, 256 rows); each step adds at most
 // 2u + 3u (a_i b_j + a_j b_i) to rho, and a direct dot product of m terms at
 // most ~2mu (1 + 14 a) (centring offsets within 8 columns), u = 2^-24.  The
 // bound doubles that sum.
@@ -179,7 +189,7 @@ __device__ __forceinline__ float eps_bound(int32_t m, const LaneState& s) {
     const float u = 5.9604644775390625e-08f;
     const float amax = __uint_as_float(__ldcg(&s.ab[0]));
     const float bmax = __uint_as_float(__ldcg(&s.ab[1]));
-    const float rec = float(kStripH - 1) * (2.f + 6.f * amax * bmax);
+    const float rec = float(kRefineHTall - 1) * (2.f + 6.f * amax * bmax);
     const float dir = 2.f * float(m + 4) * (1.f + 14.f * amax);
     // top-row seeds from the tensor cores carry their own bound (0 otherwise)
     return 2.f * u * (rec + dir + 32.f) + __uint_as_float(__ldcg(&s.seed_eps));
@@ -217,6 +227,7 @@ cudaError_t launch_seeds(const Pass& p, int sms, cudaStream_t s);
 cudaError_t launch_refine_tc(const Pass& p, int sms, cudaStream_t s);
 cudaError_t launch_recheck(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_round_cleanup(const Pass& p, cudaStream_t s);
+cudaError_t launch_shard_out(const Pass& p, cudaStream_t s);
 cudaError_t launch_gather(const Pass& p, cudaStream_t s);
 cudaError_t launch_topk(const Pass& p, cudaStream_t s);
 cudaError_t launch_finalize(const Pass& p, cudaStream_t s);

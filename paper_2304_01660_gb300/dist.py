@@ -5,13 +5,15 @@ Discord discovery shards in two ways:
 * independent series (the batched multi-series entry) split across ranks
   with no data-path collective -- each rank runs MERLIN on its own series
   (weak scaling);
-* one long series could split its pair space across ranks, with one
-  exchange per DRAG phase: a bitwise AND of the candidate bitmaps after
-  select (a window pruned by any rank is pruned) and an elementwise minimum
-  of the survivors' nearest-neighbour distances after refine (each rank saw
-  a slice of the columns).  These are the exchange steps of the cluster DRAG
-  the paper cites as related work (Sec. 1); the primitives below implement
-  them on torch.distributed, and the tests run them on CPU ranks.
+* one long series splits its pair space across ranks, with one exchange
+  per DRAG phase: a bitwise AND of the candidate bitmaps after select (a
+  window pruned by any rank is pruned) and an elementwise minimum of the
+  candidates' nearest-neighbour distances after refine (each rank saw a
+  slice of the columns).  These are the exchange steps of the cluster DRAG
+  the paper cites as related work (Sec. 1).  `sharded_drag` runs one DRAG
+  call that way through the library's shard entry points
+  (palmad_drag_select_shard / palmad_drag_refine_shard); the exchanges run
+  on torch.distributed (gloo in the tests).
 
 Timing across ranks follows the benchmark contract: the job time is the
 maximum over ranks.
@@ -68,6 +70,28 @@ def nn_min_(nn: torch.Tensor) -> torch.Tensor:
     if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
         dist.all_reduce(nn, op=dist.ReduceOp.MIN)
     return nn
+
+
+def sharded_drag(ctx, T, m: int, r: float, rank: int, world: int, options=None):
+    """One DRAG call at (m, r) split over the ranks of the default process
+    group: select over this rank's rows, bitwise AND of the candidate
+    bitmaps, refine of the common candidates against this rank's columns,
+    elementwise MIN of the results.  Every rank returns the range discords
+    (ascending indices) and their nearest-neighbour distances."""
+    import numpy as np
+    N = len(T) - m + 1
+    lo, hi = column_slice(N, rank, world)
+    bits = ctx.palmad_drag_select_shard(T, m, r, lo, hi, options)
+    bt = torch.from_numpy(bits.view(np.int32).copy())
+    candidate_and_(bt)
+    cand = bt.numpy().view(np.uint32)
+    part = ctx.palmad_drag_refine_shard(T, m, r, cand, lo, hi, options)
+    nn = torch.from_numpy(part)
+    nn_min_(nn)
+    v = nn.numpy()
+    keep = np.isfinite(v) & (v >= 0.0) & ((r <= 0.0) | (v >= r))
+    idx = np.nonzero(keep)[0]
+    return idx, v[idx]
 
 
 def column_slice(N: int, rank: int, world: int) -> tuple[int, int]:

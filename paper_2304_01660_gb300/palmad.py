@@ -47,6 +47,9 @@ class Options(ctypes.Structure):
         ("refine_seg", ctypes.c_int32),
         ("knn_k", ctypes.c_int32),
         ("no_hints", ctypes.c_int32),
+        ("spec_scale", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
+        ("refine_rows", ctypes.c_int32),
     ]
 
 
@@ -74,6 +77,7 @@ class Stats(ctypes.Structure):
         ("hint_kills", ctypes.c_int64),
         ("refine_strips", ctypes.c_int64),
         ("sweep_survivors", ctypes.c_int64),
+        ("tune_ms", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -82,6 +86,20 @@ class Stats(ctypes.Structure):
         d["kernel_ms"] = {KERNELS[i]: float(self.kernel_ms[i]) for i in range(12)}
         return d
 
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_int32),
+        ("candidates", ctypes.c_int32),
+        ("block_lo", ctypes.c_int32),
+        ("block_hi", ctypes.c_int32),
+        ("tune_ms", ctypes.c_double),
+        ("best_ms", ctypes.c_double),
+        ("default_ms", ctypes.c_double),
+    ]
+
+
+TUNED_FIELDS = ("batch_lengths", "spec_scale", "select_cap", "refine_seg", "direct_below", "refine_rows")
 
 _lib = None
 _vp = ctypes.c_void_p
@@ -117,13 +135,21 @@ def load(path: str = LIB_PATH):
                                 ctypes.POINTER(Options), _vp, _vp, ctypes.c_int64, _i64p]
     lib.palmad_topk_profile_noalloc.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                 ctypes.c_int32, _vp, _vp, _vp, _vp]
+    lib.palmad_schedule_inputs.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp]
+    lib.palmad_drag_select_shard.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                             ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Options), _vp]
+    lib.palmad_drag_refine_shard.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, _vp,
+                                             ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(Options), _vp]
+    lib.palmad_autotune.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.POINTER(Options), ctypes.POINTER(Options), ctypes.POINTER(TuneReport)]
     lib.palmad_measure_peak.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
     lib.palmad_discord_interest.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
     for name in ("palmad_default_options", "palmad_create", "palmad_get_stats", "palmad_find_discords",
                  "palmad_find_discords_device", "palmad_find_discords_batch", "palmad_drag",
                  "palmad_topk_profile_noalloc", "palmad_measure_peak", "palmad_discord_interest",
-                 "palmad_find_discords_resume"):
+                 "palmad_find_discords_resume", "palmad_autotune", "palmad_drag_select_shard",
+                 "palmad_drag_refine_shard", "palmad_schedule_inputs"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -155,8 +181,10 @@ def palmad_topk_profile_noalloc(nn_dev, m: int, r: float, K: int, exclusive: boo
     nn = torch.empty(K, dtype=torch.float64, device=dev)
     cnt = torch.empty(1, dtype=torch.int64, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
-    st = load().palmad_topk_profile_noalloc(nn_dev.data_ptr(), nn_dev.numel(), m, float(r), K, int(bool(exclusive)),
-                                            idx.data_ptr(), nn.data_ptr(), cnt.data_ptr(), s)
+    with torch.cuda.device(dev):  # the entry runs on (and caches its scratch address for) the current device
+        st = load().palmad_topk_profile_noalloc(nn_dev.data_ptr(), nn_dev.numel(), m, float(r), K,
+                                                int(bool(exclusive)), idx.data_ptr(), nn.data_ptr(),
+                                                cnt.data_ptr(), s)
     if st != PALMAD_OK:
         raise PalmadError(st, "palmad_topk_profile_noalloc failed")
     return idx, nn, cnt
@@ -183,15 +211,18 @@ def palmad_discord_interest(heat_dev, minL: int, K: int, exclusive: bool = True,
 
 
 def schedule_inputs(idx, nn) -> np.ndarray:
-    """Per length, the value the schedule of Algorithm 1 carries to the next
-    lengths: nnDist of the K-th pick, of the last pick when fewer, 0 when
-    none (idx / nn: [L, K] results).  A checkpoint at length m0 of a run
-    that started at minL is schedule_inputs(...)[max(0, l0 - 5):l0],
+    """palmad_schedule_inputs: per length, the value the schedule carries to
+    the next lengths (idx / nn: [L, K] results).  A checkpoint at length m0
+    of a run that started at minL is schedule_inputs(...)[max(0, l0 - 5):l0],
     l0 = m0 - minL."""
-    idx = np.asarray(idx)
-    nn = np.asarray(nn, dtype=np.float64)
-    got = (idx >= 0).sum(axis=1)
-    return np.where(got > 0, nn[np.arange(len(nn)), np.maximum(got - 1, 0)], 0.0)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    nn = np.ascontiguousarray(nn, dtype=np.float64)
+    L, K = idx.shape
+    out = np.empty(L, dtype=np.float64)
+    st = load().palmad_schedule_inputs(_ptr(idx), _ptr(nn), L, K, _ptr(out))
+    if st != PALMAD_OK:
+        raise PalmadError(st, "palmad_schedule_inputs failed")
+    return out
 
 
 PEAK_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
@@ -252,15 +283,25 @@ class Context:
         return s.as_dict()
 
     def palmad_find_discords(self, T, minL: int, maxL: int, topK: int, options: Options | None = None,
-                             heatmap: bool = False) -> dict:
-        """Host-memory MERLIN over one series; see palmad_find_discords in palmad.h."""
+                             heatmap: bool = False, heat_out=None) -> dict:
+        """Host-memory MERLIN over one series; see palmad_find_discords in palmad.h.
+        heat_out: optional float32 [L, n - minL + 1] array (e.g. pinned) the
+        heatmap is written into."""
         T = np.ascontiguousarray(T, dtype=np.float32)
         L = maxL - minL + 1
         idx = np.empty((L, topK), dtype=np.int64)
         nn = np.empty((L, topK), dtype=np.float64)
         cnt = np.empty(L, dtype=np.int64)
         rr = np.empty(L, dtype=np.float64)
-        heat = np.empty((L, len(T) - minL + 1), dtype=np.float32) if heatmap else None
+        heat = None
+        if heatmap:
+            shape = (L, len(T) - minL + 1)
+            if heat_out is not None:
+                if heat_out.shape != shape or heat_out.dtype != np.float32 or not heat_out.flags.c_contiguous:
+                    raise ValueError(f"heat_out must be a C-contiguous float32 array of shape {shape}")
+                heat = heat_out
+            else:
+                heat = np.empty(shape, dtype=np.float32)
         self._check(self._lib.palmad_find_discords(
             self._h, _ptr(T), len(T), minL, maxL, topK, ctypes.byref(options) if options else None,
             _ptr(idx), _ptr(nn), _ptr(cnt), _ptr(rr), _ptr(heat)))
@@ -307,6 +348,21 @@ class Context:
             rr.data_ptr(), heatmap_dev.data_ptr() if heatmap_dev is not None else None))
         return {"idx": idx, "nn": nn, "count": cnt, "r": rr}
 
+    def palmad_autotune(self, T_dev, minL: int, maxL: int, topK: int, base: Options | None = None):
+        """Tuned options for this series and length range (T_dev: float32
+        CUDA tensor) and the tuner's report as a dict."""
+        import torch
+        assert T_dev.is_cuda and T_dev.dtype == torch.float32 and T_dev.is_contiguous()
+        out = Options()
+        rep = TuneReport()
+        rep.struct_size = ctypes.sizeof(TuneReport)
+        self._check(self._lib.palmad_autotune(self._h, T_dev.data_ptr(), T_dev.numel(), minL, maxL, topK,
+                                              ctypes.byref(base) if base else None, ctypes.byref(out),
+                                              ctypes.byref(rep)))
+        report = {k: getattr(rep, k) for k, _ in rep._fields_ if k != "struct_size"}
+        report["chosen"] = {k: getattr(out, k) for k in TUNED_FIELDS}
+        return out, report
+
     def palmad_find_discords_batch(self, series, minL, maxL, topK: int, options: Options | None = None) -> list:
         """Independent series in one call; returns one result dict per series."""
         count = len(series)
@@ -326,6 +382,26 @@ class Context:
             arr([o["idx"] for o in outs]), arr([o["nn"] for o in outs]),
             arr([o["count"] for o in outs]), arr([o["r"] for o in outs])))
         return outs
+
+    def palmad_drag_select_shard(self, T, m: int, r: float, row_lo: int, row_hi: int,
+                                 options: Options | None = None) -> np.ndarray:
+        """Candidate bitmap (uint32 words) of select over rows [row_lo, row_hi)."""
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        bits = np.empty((len(T) - m + 1 + 31) // 32, dtype=np.uint32)
+        self._check(self._lib.palmad_drag_select_shard(self._h, _ptr(T), len(T), m, float(r), row_lo, row_hi,
+                                                       ctypes.byref(options) if options else None, _ptr(bits)))
+        return bits
+
+    def palmad_drag_refine_shard(self, T, m: int, r: float, cand_bits, col_lo: int, col_hi: int,
+                                 options: Options | None = None) -> np.ndarray:
+        """Per-window result of refining the candidates against columns
+        [col_lo, col_hi): -1 pruned, else the FP64 distance over those columns."""
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        bits = np.ascontiguousarray(cand_bits, dtype=np.uint32)
+        out = np.empty(len(T) - m + 1, dtype=np.float64)
+        self._check(self._lib.palmad_drag_refine_shard(self._h, _ptr(T), len(T), m, float(r), _ptr(bits), col_lo,
+                                                       col_hi, ctypes.byref(options) if options else None, _ptr(out)))
+        return out
 
     def palmad_drag(self, T, m: int, r: float, options: Options | None = None):
         """All range discords of length m at threshold r (ascending index)."""

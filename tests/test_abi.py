@@ -30,7 +30,7 @@ def test_header_declares_the_boundary():
     names = _declared()
     for want in ["palmad_create", "palmad_destroy", "palmad_find_discords", "palmad_find_discords_device",
                  "palmad_find_discords_batch", "palmad_drag", "palmad_last_error", "palmad_default_options",
-                 "palmad_get_stats", "palmad_version"]:
+                 "palmad_get_stats", "palmad_version", "palmad_autotune"]:
         assert want in names
 
 
@@ -48,6 +48,8 @@ def test_default_options_and_version(lib):
     # nearest-neighbour distance
     assert (o.precision, o.batch_lengths, o.select_cap, o.pool_slots, o.refine_seg, o.knn_k) == (0, 0, 0, 0, 0, 0)
     assert (o.direct_below, o.tc_seed_min, o.seed_rows_max, o.profile) == (0, 0, 0, 0)
+    # witness hints on, the batched margins as documented, no autotuning
+    assert (o.no_hints, o.spec_scale, o.autotune) == (0, 0, 0)
     assert palmad.palmad_default_options(knn_k=3, batch_lengths=16).knn_k == 3
     with pytest.raises(KeyError):
         palmad.palmad_default_options(no_such_option=1)
@@ -66,21 +68,25 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "palmad.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(palmad_options), offsetof(palmad_options, band_rel),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(palmad_options),
+         offsetof(palmad_options, band_rel),
          offsetof(palmad_options, profile), sizeof(palmad_stats), offsetof(palmad_stats, max_fp32_rho_err),
          offsetof(palmad_stats, kernel_ms), offsetof(palmad_stats, refine_flops),
          offsetof(palmad_options, direct_below), offsetof(palmad_options, refine_seg),
-         offsetof(palmad_stats, seed_flops), offsetof(palmad_options, knn_k));
+         offsetof(palmad_stats, seed_flops), offsetof(palmad_options, knn_k),
+         offsetof(palmad_options, autotune), offsetof(palmad_stats, tune_ms), offsetof(palmad_stats, hint_kills),
+         sizeof(palmad_tune_report), offsetof(palmad_tune_report, default_ms));
   return 0;
 }
 """)
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(probe), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    O, S = palmad.Options, palmad.Stats
+    O, S, R = palmad.Options, palmad.Stats, palmad.TuneReport
     assert got == [ctypes.sizeof(O), O.band_rel.offset, O.profile.offset, ctypes.sizeof(S),
                    S.max_fp32_rho_err.offset, S.kernel_ms.offset, S.refine_flops.offset,
-                   O.direct_below.offset, O.refine_seg.offset, S.seed_flops.offset, O.knn_k.offset]
+                   O.direct_below.offset, O.refine_seg.offset, S.seed_flops.offset, O.knn_k.offset,
+                   O.autotune.offset, S.tune_ms.offset, S.hint_kills.offset, ctypes.sizeof(R), R.default_ms.offset]
 
 
 def test_create_without_gpu_fails_cleanly(lib):

@@ -107,6 +107,26 @@ def test_drag_select_cap_does_not_change_results(ctx, cap):
     _check_drag(ctx, T, 50, r, _opts(select_cap=cap))
 
 
+@pytest.mark.parametrize("name", list(SERIES))
+@pytest.mark.parametrize("m", [8, 100])
+def test_drag_tall_refine_strips_match_oracle(ctx, name, m):
+    """256-row refine strips (refine_rows = 256): rows up to 255 recurrence
+    steps from a direct dot product, every survivor through the sweep."""
+    T = SERIES[name]()
+    mp, _ = oracle.matrix_profile(T, m)
+    for r in _thresholds(mp, (0.5, 0.95, 1.0)):
+        _check_drag(ctx, T, m, r, _opts(refine_rows=256, direct_below=1))
+        _check_drag(ctx, T, m, r, _opts(refine_rows=256, precision=1))
+
+
+def test_drag_hints_off_matches_oracle(ctx):
+    T = SERIES["sine4000"]()
+    for m in (37, 100):
+        mp, _ = oracle.matrix_profile(T, m)
+        for r in _thresholds(mp, (0.9, 0.99)):
+            _check_drag(ctx, T, m, r, _opts(no_hints=1))
+
+
 def test_drag_golden_fixtures(ctx):
     for case in json.load(open(os.path.join(HERE, "golden", "drag_random_walk.json"))):
         T = synth.random_walk(case["n"], case["seed"])
@@ -180,7 +200,9 @@ def test_refine_rounds_match_oracle(ctx, W):
 def test_merlin_options_do_not_change_results(ctx):
     T = SERIES["rw3000"]()
     base = ctx.palmad_find_discords(T, 12, 20, 2)
-    for o in (_opts(band_rel=0.05), _opts(band_rel=1e-6), _opts(select_cap=1), _opts(profile=1)):
+    for o in (_opts(band_rel=0.05), _opts(band_rel=1e-6), _opts(select_cap=1), _opts(profile=1),
+              _opts(no_hints=1), _opts(refine_rows=256), _opts(batch_lengths=8, spec_scale=10),
+              _opts(batch_lengths=8, spec_scale=400)):
         _check_merlin(ctx.palmad_find_discords(T, 12, 20, 2, o), base)
 
 

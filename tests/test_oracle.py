@@ -219,6 +219,25 @@ def test_range_discords_match_python_brute_force(n, m, seed):
         np.testing.assert_allclose(nn, ref[idx], rtol=1e-9, atol=1e-9)
 
 
+def test_range_discord_windows_is_the_same_test():
+    T = _rw(800, 16)
+    m = 20
+    mp, _ = oracle.matrix_profile(T, m)
+    r = float(np.quantile(mp[np.isfinite(mp)], 0.9))
+    idx, nn = oracle.range_discords(T, m, r)
+    wins = np.arange(0, len(T) - m + 1, 7)
+    got = oracle.range_discord_windows(T, m, r, wins)
+    want = np.full(len(wins), np.nan)
+    pos = {int(i): v for i, v in zip(idx, nn)}
+    for q, i in enumerate(wins):
+        if int(i) in pos:
+            want[q] = pos[int(i)]
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(want))
+    np.testing.assert_array_equal(got[~np.isnan(got)], want[~np.isnan(want)])
+    with pytest.raises(ValueError):
+        oracle.range_discord_windows(T, m, r, [len(T)])
+
+
 def test_drag_on_sine_finds_injected_anomaly():
     n, m = 3000, 40
     x = synth.noisy_sine(n, 50.0, 0.05, seed=3, anomalies=[(1500, 45)])
