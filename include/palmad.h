@@ -288,7 +288,7 @@ palmad_status palmad_find_discords_batch(palmad_ctx *ctx, int32_t count, const f
  * lengths per pass (batch_lengths) and the batched form's speculation margin
  * (spec_scale), the select cap, the refine segment and the refine-form split
  * (direct_below) and the refine strip height (refine_rows) -- by timing
- * candidates one setting at a time on blocks of up to 16 lengths at the
+ * candidates one setting at a time on blocks of up to 12 lengths at the
  * start, a third, two thirds and the end of [minL, maxL] of the caller's
  * series; every block after the first resumes from the schedule inputs of
  * its preceding lengths, so it meets the thresholds the whole run meets.

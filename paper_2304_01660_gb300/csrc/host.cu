@@ -501,7 +501,7 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     CK(cudaMemcpyAsync(ctx->st.p, ctx->h_st, sizeof(LaneState) * nl, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->chain.p, ctx->h_chain, sizeof(int32_t) * nchains, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(ctx->small.p, 0, sizeof(Small), ctx->stream));
-    LAUNCH(PALMAD_K_STATS, launch_stats(p, ctx->chain.p, nchains, nmax, ctx->stream));
+    LAUNCH(PALMAD_K_STATS, launch_stats(p, ctx->chain.p, nchains, nmax, ctx->sms, ctx->stream));
     if (strips > 0) LAUNCH(PALMAD_K_SELECT, launch_select(p, ctx->sms * 4, ctx->stream));
     if (io.mode == kSelect) {
         const Lane& L0 = ctx->h_lanes[0];
@@ -1153,13 +1153,13 @@ palmad_status tune(palmad_ctx* ctx, const float* T_dev, int64_t n, int32_t minL,
     palmad_options cur = base;
     cur.autotune = 0;
     cur.profile = 0;
-    // Blocks of up to 16 lengths at the start, a third, two thirds and the
+    // Blocks of up to 12 lengths at the start, a third, two thirds and the
     // end of the range.  Each later block resumes from the schedule inputs
     // of its five preceding lengths, found by a short untimed run started at
     // the first of them: a length's picks (and so its schedule input) do not
     // depend on the thresholds tried, so the block then follows the very
     // thresholds the whole run meets there.
-    const int32_t B = std::min<int32_t>(L, 16);
+    const int32_t B = std::min<int32_t>(L, 12);
     std::vector<Block> blocks;
     for (int q = 0; q < 4; ++q) {
         const int32_t lo = minL + int32_t(int64_t(L - B) * q / 3);
@@ -1229,7 +1229,7 @@ palmad_status tune(palmad_ctx* ctx, const float* T_dev, int64_t n, int32_t minL,
     // select cap
     {
         const palmad_options start = cur;
-        for (int32_t cap : {512, 2048}) {
+        for (int32_t cap : {512, 2048, 4096}) {
             palmad_options o = start;
             o.select_cap = cap;
             CKS(consider(o));
@@ -1254,7 +1254,7 @@ palmad_status tune(palmad_ctx* ctx, const float* T_dev, int64_t n, int32_t minL,
     // strips below this many survivors take the direct form
     {
         const palmad_options start = cur;
-        for (int32_t db : {2, 4, 8}) {
+        for (int32_t db : {4, 8, 16, 32, 64, 129}) {
             palmad_options o = start;
             o.direct_below = db;
             CKS(consider(o));

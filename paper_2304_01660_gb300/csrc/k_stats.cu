@@ -154,11 +154,12 @@ cudaError_t launch_stats_init(const float* T, int64_t n, int32_t m, double* mu, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_stats(const Pass& p, const int32_t* chain_first, int32_t nchains, int64_t nmax, cudaStream_t s) {
+cudaError_t launch_stats(const Pass& p, const int32_t* chain_first, int32_t nchains, int64_t nmax, int sms,
+                         cudaStream_t s) {
     if (nchains <= 0) return cudaSuccess;
     const int block = 256;
     int64_t gx = (nmax + block - 1) / block;
-    if (gx > 152 * 8) gx = 152 * 8;
+    if (gx > int64_t(sms) * 8) gx = int64_t(sms) * 8;  // 8 CTAs per SM cover every chain
     k_stats<<<dim3(unsigned(gx), unsigned(nchains)), block, 0, s>>>(p, chain_first);
     return cudaGetLastError();
 }

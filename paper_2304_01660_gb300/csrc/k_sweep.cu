@@ -96,23 +96,6 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
     return r;
 }
 
-// Packed FP32 pairs (two lanes of one 64-bit register): the seed pass below
-// issues its multiply-adds two at a time with fma.rn.f32x2 (sm_100 and
-// later), each lane rounded exactly as fmaf rounds it.
-__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
-}
-__device__ __forceinline__ float hsum2(unsigned long long v) {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return lo + hi;
-}
-
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -153,11 +136,9 @@ __device__ __forceinline__ void chunk_seeds(const LaneView& a, const WarpSmem& s
     for (int x = lane; x < kp + 32; x += 32) tw[x] -= b0;
     __syncwarp();
     const int g = lane & 3, ks = lane >> 2;
-    // column c accumulates its four k terms of a block as two packed pairs:
-    // (k, k+1) x (x[c], x[c+1]) and (k+2, k+3) x (x[c+2], x[c+3])
-    unsigned long long acc2[8];
+    float acc[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc2[c] = 0ull;
+    for (int c = 0; c < 8; ++c) acc[c] = 0.f;
     const float* ap = sm.ahat + 4 * ks;
     const float* tp = tw + 8 * g + 4 * ks;
     for (int q = 0; q < kp; q += 32) {
@@ -165,20 +146,13 @@ __device__ __forceinline__ void chunk_seeds(const LaneView& a, const WarpSmem& s
         const float4 t0 = *reinterpret_cast<const float4*>(tp + q);
         const float4 t1 = *reinterpret_cast<const float4*>(tp + q + 4);
         const float4 t2 = *reinterpret_cast<const float4*>(tp + q + 8);
-        const float tv[11] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x, t2.y, t2.z};
-        const unsigned long long a01 = pk2(av.x, av.y), a23 = pk2(av.z, av.w);
-        unsigned long long xp[10];  // xp[i] = (x[i], x[i+1])
+        const float a4[4] = {av.x, av.y, av.z, av.w};
+        const float tv[12] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x, t2.y, t2.z, t2.w};
 #pragma unroll
-        for (int i = 0; i < 10; ++i) xp[i] = pk2(tv[i], tv[i + 1]);
+        for (int qq = 0; qq < 4; ++qq)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            ffma2(acc2[c], a01, xp[c]);
-            ffma2(acc2[c], a23, xp[c + 2]);
-        }
+            for (int c = 0; c < 8; ++c) acc[c] = fmaf(a4[qq], tv[qq + c], acc[c]);
     }
-    float acc[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = hsum2(acc2[c]);
     const float dot = reduce_scatter8(acc, lane);
     const int col = g * 8 + ks;
     const int64_t j = c0 + col;

@@ -213,7 +213,8 @@ __device__ __forceinline__ int lane_of(const int64_t* base, int nl, int64_t item
 // Launchers (each returns the launch's cudaError_t).
 cudaError_t launch_stats_init(const float* T, int64_t n, int32_t m, double* mu, double* var, int32_t* flags,
                               cudaStream_t s);
-cudaError_t launch_stats(const Pass& p, const int32_t* chain_first, int32_t nchains, int64_t nmax, cudaStream_t s);
+cudaError_t launch_stats(const Pass& p, const int32_t* chain_first, int32_t nchains, int64_t nmax, int sms,
+                         cudaStream_t s);
 cudaError_t launch_select(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_compact(const Pass& p, cudaStream_t s);
 bool hint_supported(const Pass& p);
