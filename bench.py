@@ -296,8 +296,9 @@ def run_ours(args, w):
     # or given with --options (profiling runs)
     mixed_base = palmad.palmad_default_options(precision=1, batch_lengths=args.batch)
     if args.options:
-        kv = dict(item.split("=") for item in args.options.split(","))
-        tuned = palmad.palmad_default_options(precision=1, **{k: int(v) for k, v in kv.items()})
+        kv = {"precision": 1}
+        kv.update({k: int(v) for k, v in (item.split("=") for item in args.options.split(","))})
+        tuned = palmad.palmad_default_options(**kv)
         tune_rep = {"tune_ms": 0.0, "candidates": 0, "block_lo": 0, "block_hi": 0, "best_ms": None, "default_ms": None,
                     "chosen": {k: getattr(tuned, k) for k in palmad.TUNED_FIELDS}, "given": args.options}
     else:
@@ -307,6 +308,9 @@ def run_ours(args, w):
         "mixed_tuned": tuned,
         "plain": palmad.palmad_default_options(profile=prof),
         f"mixed_w{args.batch}": palmad.palmad_default_options(profile=prof, precision=1, batch_lengths=args.batch),
+        # the k-th neighbour variant (k = 2) with the tuned configuration (its own form; off by default)
+        "knn2": palmad.palmad_default_options(**{**{k: getattr(tuned, k) for k in palmad.TUNED_FIELDS},
+                                                 "profile": prof, "knn_k": 2}),
     }
     forms = {f: o for f, o in forms.items() if f == "mixed_tuned" or f.split("_")[0] in args.forms.split(",")}
     chosen = tune_rep["chosen"]
@@ -363,7 +367,7 @@ def run_ours(args, w):
     R = results["mixed_tuned"]
     ref_out = R["out"]
     parity["forms_identical"] = all(
-        all(np.array_equal(ref_out[k], r["out"][k]) for k in ref_out) for r in results.values())
+        all(np.array_equal(ref_out[k], r["out"][k]) for k in ref_out) for f, r in results.items() if f != "knn2")
     total_ms = R["total_ms"]
     value = units * args.steps * world / (total_ms / 1e3)
     last_stats = R["stats"]
@@ -441,7 +445,9 @@ def run_ours(args, w):
                                f"(lengths per pass {max(1, chosen['batch_lengths'])}, speculation margin "
                                f"{chosen['spec_scale'] or 100}%, select cap {chosen['select_cap'] or 1024}, refine "
                                f"segment {chosen['refine_seg'] or 'auto'}, direct form below "
-                               f"{chosen['direct_below'] or 'auto'} survivors, refine strips of "
+                               f"{chosen['direct_below'] or 'auto'} survivors (windows up to 256; "
+                               f"{chosen['direct_below_long'] or chosen['direct_below'] or 'auto'} for longer), "
+                               f"refine strips of "
                                f"{chosen['refine_rows'] or 128} rows)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
@@ -496,7 +502,9 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=16, help="lengths per pass of the untuned batched form")
     ap.add_argument("--side-steps", type=int, default=2,
                     help="timed steps of the secondary forms and of the end-to-end leg")
-    ap.add_argument("--forms", default="plain,mixed", help="secondary forms to time beside the tuned one")
+    ap.add_argument("--forms", default="plain,mixed",
+                    help="secondary forms to time beside the tuned one: plain, mixed (16 lengths per pass), "
+                         "knn2 (the k-th neighbour variant, k = 2)")
     ap.add_argument("--options", default=None,
                     help="k=v,...: options of the headline form instead of the autotuner's (profiling runs)")
     ap.add_argument("--lengths", default=None,

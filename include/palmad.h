@@ -134,6 +134,9 @@ typedef struct {
     int32_t refine_rows;     /* rows per strip of the recurrence-form refine: 0 or 128
                                 (default), or 256 (half the top-row dot products per row,
                                 strips live until their last survivor is decided) */
+    int32_t direct_below_long; /* as direct_below, for passes whose windows are longer than
+                                256 (0 = direct_below): the direct form costs 2m flops per
+                                survivor-column, so the best split depends on m */
 } palmad_options;
 
 /* Per-call counters of the most recent find/drag call. */
@@ -287,7 +290,7 @@ palmad_status palmad_find_discords_batch(palmad_ctx *ctx, int32_t count, const f
  * chooses the pass configuration for one series and length range --
  * lengths per pass (batch_lengths) and the batched form's speculation margin
  * (spec_scale), the select cap, the refine segment and the refine-form split
- * (direct_below) and the refine strip height (refine_rows) -- by timing
+ * (direct_below, direct_below_long) and the refine strip height (refine_rows) -- by timing
  * candidates one setting at a time on blocks of up to 12 lengths at the
  * start, a third, two thirds and the end of [minL, maxL] of the caller's
  * series; every block after the first resumes from the schedule inputs of

@@ -36,6 +36,7 @@ namespace {
 
 constexpr int kDefaultCap = 1024;    // select columns past the strip triangle
 constexpr double kPairFlops = 8.0;   // algorithmic FP32 flops of one recurrence-form pair evaluation
+constexpr int32_t kLongWindow = 256;  // kpad above which a pass uses direct_below_long
 constexpr int kRefineSeg = 1024;      // refine sweep columns per work item (multiple of 256) ...
 constexpr int kRefineSegLong = 2048;  // ... and for passes with many columns (lanes x N >= kLongPass)
 constexpr int64_t kLongPass = 2000000;
@@ -110,7 +111,7 @@ struct palmad_ctx {
     // refine pool
     int32_t pool = 0;
     int32_t pool_kpad = 0, pool_nchunks = 0;
-    DBuf<int32_t> slot_lane, slot_win, route, dlist, dgroups, dead, strip_row;
+    DBuf<int32_t> slot_lane, slot_win, route, dlist, dgroups, dead, kcnt, strip_row;
     DBuf<float> topcen, topsum, seeds;
     DBuf<int4> seed_groups;
     bool sets_dirty = false;       // a pass stopped early: slot maps may not be clean
@@ -275,6 +276,7 @@ palmad_status read_options(palmad_ctx* ctx, const palmad_options* in, palmad_opt
     if (o.no_hints != 0 && o.no_hints != 1) return fail(ctx, PALMAD_ERR_ARG, "no_hints must be 0 or 1");
     if (o.spec_scale < 0 || o.spec_scale > 400) return fail(ctx, PALMAD_ERR_ARG, "spec_scale must lie in [0, 400]");
     if (o.autotune != 0 && o.autotune != 1) return fail(ctx, PALMAD_ERR_ARG, "autotune must be 0 or 1");
+    if (o.direct_below_long < 0) return fail(ctx, PALMAD_ERR_ARG, "direct_below_long must be >= 0");
     if (o.refine_rows != 0 && o.refine_rows != kRefineH && o.refine_rows != kRefineHTall)
         return fail(ctx, PALMAD_ERR_ARG, "refine_rows must be 0, 128 or 256");
     return PALMAD_OK;
@@ -344,7 +346,7 @@ palmad_status ensure_pool(palmad_ctx* ctx, int32_t kpad, int32_t nchunks) {
     slots = std::max<int64_t>(64, (slots / 64) * 64);
     CKS(ensure(ctx, ctx->slot_lane, slots)); CKS(ensure(ctx, ctx->slot_win, slots)); CKS(ensure(ctx, ctx->route, slots));
     CKS(ensure(ctx, ctx->dlist, slots)); CKS(ensure(ctx, ctx->dgroups, slots / 64 + 1));
-    CKS(ensure(ctx, ctx->dead, slots)); CKS(ensure(ctx, ctx->asum, slots)); CKS(ensure(ctx, ctx->gmax, slots));
+    CKS(ensure(ctx, ctx->dead, slots)); CKS(ensure(ctx, ctx->kcnt, slots)); CKS(ensure(ctx, ctx->asum, slots)); CKS(ensure(ctx, ctx->gmax, slots));
     CKS(ensure(ctx, ctx->nn2, slots));
     CKS(ensure(ctx, ctx->acen, size_t(slots) * kpad));
     CKS(ensure(ctx, ctx->cmax, size_t(slots) * nchunks));
@@ -376,6 +378,7 @@ Pass base_pass(palmad_ctx* ctx, int nl, int K, bool exclusive, const palmad_opti
     p.asum = ctx->asum.p;
     p.gmax = ctx->gmax.p;
     p.dead = ctx->dead.p;
+    p.kcnt = ctx->kcnt.p;
     p.nn2 = ctx->nn2.p;
     p.cmax = ctx->cmax.p;
     p.cmax2 = ctx->cmax2.p;
@@ -421,8 +424,9 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
         L.nstrips = int32_t(std::max<int64_t>(0, std::min<int64_t>((L.N + kStripH - 1) / kStripH, L.strip_lim) -
                                                   L.strip0));
         L.strip_base = strips;
-        strips += L.prune ? L.nstrips : 0;
-        if (!L.prune) L.nstrips = 0;
+        const bool sel = L.prune && o.knn_k <= 1;  // select prunes on one pair: nearest neighbour only
+        strips += sel ? L.nstrips : 0;
+        if (!sel) L.nstrips = 0;
         kpad_max = std::max(kpad_max, L.kpad);
         nchunks_max = std::max<int32_t>(nchunks_max, int32_t((L.N + 31) / 32));
         nmax = std::max(nmax, L.N);
@@ -472,7 +476,10 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     // when asked (the autotuner's refine_rows), never with tensor-core seeds
     p.refine_h = (o.refine_rows == kRefineHTall && !(o.precision == PALMAD_PREC_MIXED && o.tc_seed_min > 0))
                      ? kRefineHTall : kRefineH;
-    p.direct_below = o.direct_below;
+    // passes of long windows (kpad > 256) may split their strips differently:
+    // the direct form costs 2m flops per survivor-column, the sweep's top-row
+    // seed as much per strip-column on top of 8 per row
+    p.direct_below = (kpad_max > kLongWindow && o.direct_below_long > 0) ? o.direct_below_long : o.direct_below;
     p.strip_row = ctx->strip_row.p;
     p.seed_ngroups = &ctx->small.p->seed_ngroups;
     p.tc_seeds = 0;
@@ -525,7 +532,7 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
         // witness hints: survivors pruned by a pair near where an earlier
         // length pruned them leave before refine; the survivor list is rebuilt
         bool hinted = false;
-        for (int l = 0; l < nl; ++l) hinted |= ctx->h_lanes[l].hint != nullptr && ctx->h_lanes[l].prune;
+        for (int l = 0; l < nl; ++l) hinted |= ctx->h_lanes[l].hint != nullptr && ctx->h_lanes[l].prune && p.knn <= 1;
         if (hinted && hint_supported(p)) {
             LAUNCH(PALMAD_K_HINT, launch_hint(p, ctx->sms, ctx->stream));
             LAUNCH(PALMAD_K_COMPACT, launch_compact(p, ctx->stream));
@@ -774,8 +781,9 @@ Lane make_lane(palmad_ctx* ctx, SeriesJob& s, int32_t li, double r, const palmad
     L.strip_lim = INT64_MAX;
     L.col_lo = 0;
     L.col_hi = L.N;
-    // k-th neighbour variant: no single pair decides, every window is refined
-    L.prune = (r > 0.0 && o.knn_k <= 1) ? 1 : 0;
+    // k-th neighbour variant: refine prunes a window at its k-th pair past the
+    // threshold; select (one pair decides there) is skipped
+    L.prune = r > 0.0 ? 1 : 0;
     L.rho_thr = float(1.0 - r * r / (2.0 * L.m));
     L.band = float(o.band_rel * r * r / L.m);
     // statistics source
@@ -1251,12 +1259,23 @@ palmad_status tune(palmad_ctx* ctx, const float* T_dev, int64_t n, int32_t minL,
         o.refine_rows = kRefineHTall;
         CKS(consider(o));
     }
-    // strips below this many survivors take the direct form
+    // strips below this many survivors take the direct form: one threshold
+    // for passes of windows up to 256 long, one for longer windows (the two
+    // touch disjoint passes, so each is searched on its own)
     {
+        const palmad_options start = cur;
+        for (int32_t db : {2, 4, 8, 16, 32}) {
+            palmad_options o = start;
+            o.direct_below = db;
+            o.direct_below_long = start.direct_below_long > 0 ? start.direct_below_long : start.direct_below;
+            CKS(consider(o));
+        }
+    }
+    if (maxL + 31 > kLongWindow + 32) {
         const palmad_options start = cur;
         for (int32_t db : {4, 8, 16, 32, 64, 129}) {
             palmad_options o = start;
-            o.direct_below = db;
+            o.direct_below_long = db;
             CKS(consider(o));
         }
     }
@@ -1357,6 +1376,7 @@ void palmad_destroy(palmad_ctx* ctx) {
     release(ctx->lanes); release(ctx->st); release(ctx->chain); release(ctx->small);
     release(ctx->pidx); release(ctx->pnn);
     release(ctx->slot_lane); release(ctx->slot_win); release(ctx->route); release(ctx->dlist); release(ctx->dgroups); release(ctx->dead);
+    release(ctx->kcnt);
     release(ctx->acen); release(ctx->asum); release(ctx->cmax); release(ctx->cmax2); release(ctx->gmax); release(ctx->nn2);
     release(ctx->strips); release(ctx->init_flags);
     release(ctx->strip_row); release(ctx->topcen); release(ctx->topsum); release(ctx->seeds); release(ctx->seed_groups);
@@ -1660,7 +1680,7 @@ palmad_status drag_lane(palmad_ctx* ctx, const float* T, int64_t n, int32_t m, d
     L.mu_src = S.mu.p;
     L.var_src = S.var.p;
     L.r = r;
-    L.prune = (r > 0.0 && o.knn_k <= 1) ? 1 : 0;
+    L.prune = r > 0.0 ? 1 : 0;
     L.rho_thr = float(1.0 - r * r / (2.0 * m));
     L.band = float(o.band_rel * r * r / m);
     L.strip0 = 0;

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kHintWarps * 32) k_hint(const Pass p) {
     extern __shared__ __align__(16) float smem[];
     const int l = blockIdx.y;
     const Lane& L = p.lanes[l];
-    if (!L.prune || !L.hint) return;
+    if (!L.prune || !L.hint || p.knn > 1) return;  // one pair decides nothing in the k-th neighbour variant
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int kps = p.kpad_pass;
     float* a = smem + hint_warp_floats(kps) * wid;  // [kps]               centred survivor window

@@ -94,6 +94,7 @@ __global__ void k_plan_count(const Pass p) {
         const int32_t k = L.k_lo + (g - L.slot_base);
         p.slot_lane[g] = l;
         p.dead[g] = 0;
+        p.kcnt[g] = 0;
         p.gmax[g] = 0u;
         p.nn2[g] = 0x7ff0000000000000ull;
         if (k >= L.k_hi) {
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
             const float invc = sok ? win[ci].z : 0.f;
             const float sa = sok ? p.asum[g] : 0.f;
             float mx = -kInf;
-            int np = 0;
+            int np = 0, nk = 0;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int64_t dj = jc + c - ci;
@@ -301,8 +302,13 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
                 if (has_flat && (invc == 0.f || invj[c] == 0.f)) rho = (invc == 0.f && invj[c] == 0.f) ? 1.f : 0.f;
                 mx = ok ? fmaxf(mx, rho) : mx;
                 np += ok;
+                nk += (ok && rho > rho_prune) ? 1 : 0;
             }
             pairs += np;
+            if (p.knn > 1) {  // pairs of the tile past the threshold, over the 32 lanes
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) nk += __shfl_xor_sync(kFull, nk, o);
+            }
             mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, 1));
             mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, 2));
             if ((lane & 3) == 0 && sok && jc < N) p.cmax[g * p.nchunks_max + (jc >> 5)] = mx;
@@ -313,7 +319,8 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
                     atomicMax(&p.gmax[g], enc_f32(mx));
                     atomicMax(&p.cmax2[g * p.ncoarse_max + (j0 / p.seg)], enc_f32(mx));  // tile inside one block
                 }
-                if (mx > rho_prune) {
+                const bool die = p.knn > 1 ? (nk > 0 && atomicAdd(&p.kcnt[g], nk) + nk >= p.knn) : mx > rho_prune;
+                if (die) {
                     p.dead[g] = 1;
                     if (L.hint) L.hint[ci] = int32_t(j0 + kRC / 2);  // witness hint: this tile
                 }

@@ -42,24 +42,27 @@ namespace {
 using namespace tc;
 
 constexpr int kTcM = 128;       // columns per MMA tile (TMEM lanes)
-constexpr int kTcTiles = 8;     // tiles per work item
+constexpr int kTcTiles = 8;     // tiles per work item (1024 columns) ...
+constexpr int kTcTilesLong = 16;  // ... or a whole 2048-column refine segment when shared memory allows
 constexpr int kTcThreads = 256;  // two warpgroups; each reads every TMEM lane quarter
 
 struct TcLayout {
     int kp;          // kpad_max (multiple of 32)
     int ns;          // survivors per MMA
+    int tiles;       // tiles per work item
     size_t b_bytes;  // one split of the survivor operand
     size_t a_bytes;  // one split of one Hankel buffer
     size_t off_bh, off_bl, off_ah, off_al, off_t, off_c, off_misc, total;
 };
 
 // Series floats staged per work item: its columns plus the window tail.
-__host__ __device__ constexpr int tc_span(int kp) { return kTcTiles * kTcM + kp + 16; }
+__host__ __device__ constexpr int tc_span(int kp, int tiles) { return tiles * kTcM + kp + 16; }
 
-__host__ __device__ inline TcLayout tc_layout(int kp, int ns) {
+__host__ __device__ inline TcLayout tc_layout(int kp, int ns, int tiles) {
     TcLayout t{};
     t.kp = kp;
     t.ns = ns;
+    t.tiles = tiles;
     t.b_bytes = size_t(ns) * kp * 2;
     t.a_bytes = size_t(kTcM / 8 + kp / 8) * 128;
     t.off_bh = 0;
@@ -67,21 +70,31 @@ __host__ __device__ inline TcLayout tc_layout(int kp, int ns) {
     t.off_ah = 2 * t.b_bytes;                // [2] buffers
     t.off_al = t.off_ah + 2 * t.a_bytes;     // [2] buffers
     t.off_t = t.off_al + 2 * t.a_bytes;      // series slice (FP32)
-    t.off_c = t.off_t + size_t(tc_span(kp)) * 4;  // column records (inv, mu)
-    t.off_misc = t.off_c + size_t(kTcTiles * kTcM) * 8;
+    t.off_c = t.off_t + size_t(tc_span(kp, tiles)) * 4;  // column records (inv, mu)
+    t.off_misc = t.off_c + size_t(tiles * kTcM) * 8;
     // misc: survivor records (float4), slots, lower-bound maxima; mbar[2]; tmem slot; flag
     t.total = t.off_misc + size_t(ns) * (16 + 4 + 4 + 8) + 64;
     return t;
 }
 
 // a tile lies inside one coarse block (p.seg is a multiple of 1024), and a
-// work item of kTcM * kTcTiles = 1024 columns touches one block
+// work item of 1024 columns, or of 2048 when the segment (coarse block) is
+// 2048 columns, touches one block
 static_assert(kCoarseMin % kTcM == 0 && kTcM * kTcTiles <= kCoarseMin, "tiles and items inside coarse blocks");
+
+// Tiles per work item: a whole 2048-column segment when the pass uses such
+// segments and the layout fits in shared memory (the survivor operand, staged
+// once per item, is then reused by twice as many tiles), else 1024 columns.
+__host__ __device__ inline int tc_tiles(const Pass& p, int ns) {
+    return (p.seg >= kTcTilesLong * kTcM && tc_layout(p.kpad_pass, ns, kTcTilesLong).total <= size_t(227 * 1024))
+               ? kTcTilesLong : kTcTiles;
+}
 
 template <int NS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const TcLayout lay = tc_layout(p.kpad_pass, NS);
+    const int tiles_item = tc_tiles(p, NS);
+    const TcLayout lay = tc_layout(p.kpad_pass, NS, tiles_item);
     unsigned char* bh = smem + lay.off_bh;
     unsigned char* bl = smem + lay.off_bl;
     float* s_T = reinterpret_cast<float*>(smem + lay.off_t);
@@ -98,7 +111,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
     const uint32_t idesc = instr_desc(kTcM, NS);
     const int64_t ngroups = *reinterpret_cast<volatile int32_t*>(p.work + 4);
     const int64_t nhalf = 64 / NS;  // MMA groups per 64-slot direct group
-    const int64_t nblk = (p.nmax + kTcM * kTcTiles - 1) / (kTcM * kTcTiles);
+    const int64_t nblk = (p.nmax + kTcM * tiles_item - 1) / (kTcM * tiles_item);
     const int64_t nitems = ngroups * nhalf * nblk;
 
     if (tid == 0) {
@@ -135,7 +148,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
         const int64_t N = L.N, n = L.n;
         const int32_t m = L.m, kpad = L.kpad;
         const int32_t nd = min64(NS, int64_t(S.ndirect) - (gbase - L.slot_base));
-        const int64_t jstart = blk * int64_t(kTcM * kTcTiles);
+        const int64_t jstart = blk * int64_t(kTcM * tiles_item);
         if (nd <= 0 || jstart >= N) {
             __syncthreads();
             continue;
@@ -165,7 +178,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
             __syncthreads();
             continue;
         }
-        const int ntiles = int(min64(kTcTiles, (N - jstart + kTcM - 1) / kTcM));
+        const int ntiles = int(min64(tiles_item, (N - jstart + kTcM - 1) / kTcM));
         // series slice t[jstart, jstart + span) and column records (inv, mu) of
         // the item's columns, loaded with many loads in flight
         {
@@ -224,7 +237,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
         // Epilogue of tile t (accumulator t & 1).
         auto epilogue = [&](int t) {
             const int b = t & 1;
-            if (!mbar_wait(&mbar[b], (phase >> b) & 1u)) tmo = true;
+            // one lane per warp polls the barrier (256 spinning threads would
+            // flood shared memory while the MMAs run), then the warp syncs
+            int done = 1;
+            if (lane == 0) done = mbar_wait(&mbar[b], (phase >> b) & 1u) ? 1 : 0;
+            done = __shfl_sync(0xffffffffu, done, 0);
+            __syncwarp();
+            if (!done) tmo = true;
             phase ^= 1u << b;
             fence_after();
             const int64_t j0 = jstart + int64_t(t) * kTcM;
@@ -346,7 +365,7 @@ bool refine_tc_supported(const Pass& p) { return p.kpad_pass <= 1024 && p.nmax <
 cudaError_t launch_refine_tc(const Pass& p, int sms, cudaStream_t s) {
     if (p.nslots <= 0) return cudaSuccess;
     const int ns = p.kpad_pass <= 512 ? 64 : 32;
-    const TcLayout lay = tc_layout(p.kpad_pass, ns);
+    const TcLayout lay = tc_layout(p.kpad_pass, ns, tc_tiles(p, ns));
     // at least 76 KB per CTA: at most 2 CTAs (2 x 128 TMEM columns) per SM
     const size_t smem = lay.total > 78 * 1024 ? lay.total : size_t(78 * 1024);
     cudaError_t e;

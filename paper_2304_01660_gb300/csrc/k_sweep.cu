@@ -197,7 +197,10 @@ __device__ __forceinline__ void first_col_seeds(const LaneView& a, int64_t r0, i
     }
 }
 
-template <int D, bool REFINE>
+// KNN (refine only): the k-th neighbour variant; a survivor dies once k of
+// its pairs clear the pruning threshold (counted per slot over every work
+// item), instead of at its first such pair.
+template <int D, bool REFINE, bool KNN = false>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(const Pass p) {
     constexpr int H = 32 * D;
     extern __shared__ __align__(16) float smem[];
@@ -288,6 +291,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
         // Rows of this lane.
         float df_r[D], dg_r[D], inv_r[D], thr_r[D], cov[D], rmax[D];
         int32_t slot[D];
+        int32_t kc[D];  // KNN: pairs of this chunk past the threshold, per row
+#pragma unroll
+        for (int d = 0; d < D; ++d) kc[d] = 0;
         uint32_t alive = 0;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
@@ -391,6 +397,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
                     }
                     rmax[d] = fmaxf(rmax[d], x[d]);
                     if (!REFINE) pred |= x[d] > thr_r[d];
+                    if (KNN) kc[d] += x[d] > thr_r[d] ? 1 : 0;
                 }
                 if (!REFINE && pred) colmask |= 1u << st;
             };
@@ -407,6 +414,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
 #pragma unroll
                     for (int d = 0; d < D; ++d) {
                         rmax[d] = fmax3(rmax[d], x0[d], x1[d]);
+                        if (KNN) kc[d] += (x0[d] > thr_r[d] ? 1 : 0) + (x1[d] > thr_r[d] ? 1 : 0);
                         if (!REFINE) {
                             p0 |= x0[d] > thr_r[d];
                             p1 |= x1[d] > thr_r[d];
@@ -463,13 +471,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
                         const float rho = rmax[d] > -kInf ? rmax[d] * inv_r[d] : -kInf;
                         p.cmax[int64_t(slot[d]) * p.nchunks_max + t] = rho;
                         tmax[d] = fmaxf(tmax[d], rho);
-                        if (rmax[d] > thr_r[d]) {
+                        const bool die = KNN ? (kc[d] > 0 && atomicAdd(&p.kcnt[slot[d]], kc[d]) + kc[d] >= p.knn)
+                                             : rmax[d] > thr_r[d];
+                        if (die) {
                             p.dead[slot[d]] = 1;
                             alive &= ~(1u << d);
                             if (Lg.hint) Lg.hint[r0 + d] = int32_t(c0 + 16);
                         }
                     }
                     rmax[d] = -kInf;
+                    if (KNN) kc[d] = 0;
                 }
                 alive &= ~gdead;
                 if (!__any_sync(kFull, alive)) break;
@@ -498,14 +509,15 @@ size_t sweep_smem(const Pass& p) {
     return sizeof(float) * (kp + 2 * (kp + 32) + 2 * 128 + 32 + 64) * kWarpsPerCta + sizeof(int64_t) * size_t(p.nl);
 }
 
-template <bool REFINE, int D>
+template <bool REFINE, int D, bool KNN = false>
 cudaError_t launch_sweep_impl(const Pass& p, int grid, cudaStream_t s) {
     const size_t sm = sweep_smem(p);
     if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep<D, REFINE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        cudaError_t e =
+            cudaFuncSetAttribute(k_sweep<D, REFINE, KNN>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         if (e != cudaSuccess) return e;
     }
-    k_sweep<D, REFINE><<<grid, kWarpsPerCta * 32, sm, s>>>(p);
+    k_sweep<D, REFINE, KNN><<<grid, kWarpsPerCta * 32, sm, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -516,6 +528,7 @@ cudaError_t launch_select(const Pass& p, int grid, cudaStream_t s) {
 }
 
 cudaError_t launch_refine_sweep(const Pass& p, int grid, cudaStream_t s) {
+    if (p.knn > 1) return launch_sweep_impl<true, kRefineH / 32, true>(p, grid, s);  // 128-row strips
     if (p.refine_h == kRefineHTall) return launch_sweep_impl<true, kRefineHTall / 32>(p, grid * 3 / 4, s);
     return launch_sweep_impl<true, kRefineH / 32>(p, grid, s);
 }

@@ -144,6 +144,7 @@ struct Pass {
     float* asum;           // [slots]
     uint32_t* gmax;        // [slots] enc_f32 of the maximum rho
     int32_t* dead;         // [slots]
+    int32_t* kcnt;         // [slots] k-th neighbour variant: pairs past the pruning threshold so far
     unsigned long long* nn2;  // [slots] FP64 bits of the smallest d^2
     float* cmax;           // [slots][nchunks_max] maximum rho per 32-column chunk
     uint32_t* cmax2;       // [slots][ncoarse_max] enc_f32 of the maximum per coarse block (seg columns:

@@ -50,6 +50,7 @@ class Options(ctypes.Structure):
         ("spec_scale", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
         ("refine_rows", ctypes.c_int32),
+        ("direct_below_long", ctypes.c_int32),
     ]
 
 
@@ -99,7 +100,8 @@ class TuneReport(ctypes.Structure):
     ]
 
 
-TUNED_FIELDS = ("batch_lengths", "spec_scale", "select_cap", "refine_seg", "direct_below", "refine_rows")
+TUNED_FIELDS = ("batch_lengths", "spec_scale", "select_cap", "refine_seg", "direct_below", "direct_below_long",
+                "refine_rows")
 
 _lib = None
 _vp = ctypes.c_void_p
