@@ -323,12 +323,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
                 const uint32_t d = tmem + uint32_t(b * NS);
                 const uint32_t a_h = smem_u32(ah), a_l = smem_u32(al), b_h = smem_u32(bh), b_l = smem_u32(bl);
                 const uint32_t sbo_b = 16u * uint32_t(kpad);
+                // a K step of 16 advances every operand by 256 bytes: 16 in the
+                // descriptors' start-address field (addresses stay below 2^18)
+                uint64_t dah = mat_desc(a_h, 128, 128), dal = mat_desc(a_l, 128, 128);
+                uint64_t dbh = mat_desc(b_h, 128, sbo_b), dbl = mat_desc(b_l, 128, sbo_b);
                 for (int k = 0; k < kpad / 16; ++k) {
-                    const uint64_t dah = mat_desc(a_h + 256 * k, 128, 128), dal = mat_desc(a_l + 256 * k, 128, 128);
-                    const uint64_t dbh = mat_desc(b_h + 256 * k, 128, sbo_b), dbl = mat_desc(b_l + 256 * k, 128, sbo_b);
                     mma_bf16(d, dah, dbh, idesc, k > 0);
                     mma_bf16(d, dah, dbl, idesc, 1);
                     mma_bf16(d, dal, dbh, idesc, 1);
+                    dah += 16; dal += 16; dbh += 16; dbl += 16;
                 }
                 mma_commit(&mbar[b]);
             }
