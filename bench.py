@@ -46,10 +46,11 @@ METRIC = "points x lengths / s (all lengths minL..maxL, exact discords)"
 UNIT = "points*lengths/s"
 L2_FLUSH_BYTES = 512 << 20
 FIXTURE = os.path.join(ROOT, "tests", "golden", "beats1m_windows.json")
-# DRAM bytes (read + write) per launch of a kernel, from an ncu capture of
-# the named kernel source on this workload: (sha256 of the source file,
-# bytes).  A source that no longer matches reports null.
-TRAFFIC = {}
+# DRAM bytes (read + write) per evaluated pair of a kernel, from an ncu
+# capture of a bounded case of this workload: (sha256[:16] of the kernel's
+# source file at the capture, bytes per pair).  The bench scales it to its own launches by their pair
+# counts; a source that no longer matches reports null.
+TRAFFIC: dict[str, tuple[str, float]] = {}
 
 
 def _peaks():
@@ -347,6 +348,7 @@ def run_ours(args, w):
                 acc["pairs"]["refine"] += st["refine_pairs"]
                 acc["pairs"]["fp64"] += st["fp64_pairs"]
                 acc["pairs"]["hint"] += st["hint_pairs"]
+                acc["pairs"]["direct"] = acc["pairs"].get("direct", 0) + st["direct_pairs"]
             torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -413,7 +415,10 @@ def run_ours(args, w):
                "refine_direct": "paper_2304_01660_gb300/csrc/k_refine_tc.cu" if tensor
                else "paper_2304_01660_gb300/csrc/k_refine.cu"}.get(dom, "")
         trf = TRAFFIC.get(dom if not tensor else "refine_direct_tc")
-        traffic = trf[1] if trf and trf[0] == _src_hash(src) else None
+        traffic = None
+        if trf and trf[0] == _src_hash(src) and launches_per.get(dom):
+            dpairs = pairs.get("direct", 0) if dom == "refine_direct" else pairs.get("refine", 0) - pairs.get("direct", 0)
+            traffic = trf[1] * dpairs / args.steps / launches_per[dom]
         if dom in flops and kernel_ms.get(dom, 0) > 0:
             ach = flops[dom] / (kernel_ms[dom] / 1e3) / 1e12
             if tensor:
@@ -447,7 +452,7 @@ def run_ours(args, w):
                                f"segment {chosen['refine_seg'] or 'auto'}, direct form below "
                                f"{chosen['direct_below'] or 'auto'} survivors (windows up to 256; "
                                f"{chosen['direct_below_long'] or chosen['direct_below'] or 'auto'} for longer), "
-                               f"refine strips of "
+                               f"direct refine in {chosen['tc_chunks'] or 1} column chunks, refine strips of "
                                f"{chosen['refine_rows'] or 128} rows)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},

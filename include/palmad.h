@@ -137,6 +137,12 @@ typedef struct {
     int32_t direct_below_long; /* as direct_below, for passes whose windows are longer than
                                 256 (0 = direct_below): the direct form costs 2m flops per
                                 survivor-column, so the best split depends on m */
+    int32_t tc_group;        /* mixed precision: survivors per tensor-core MMA, 0 (64, or 32
+                                for windows above 512), 32, 64, 128 (windows up to 256) or
+                                256 (windows up to 128) */
+    int32_t tc_chunks;       /* mixed precision: the direct refine of a round runs over the
+                                columns in this many chunks (0 = 1), re-packing the
+                                survivors still alive into full groups between chunks */
 } palmad_options;
 
 /* Per-call counters of the most recent find/drag call. */
@@ -169,6 +175,8 @@ typedef struct {
     int64_t refine_strips;      /* strips the recurrence-form refine swept (sum over rounds) */
     int64_t sweep_survivors;    /* survivors in those strips */
     double tune_ms;             /* autotuning done by this call (wall ms), 0 if none */
+    int64_t direct_pairs;       /* of refine_pairs, those the direct form evaluated
+                                   (FP32 or tensor cores) */
 } palmad_stats;
 
 /* What palmad_autotune timed and chose. */
@@ -290,7 +298,8 @@ palmad_status palmad_find_discords_batch(palmad_ctx *ctx, int32_t count, const f
  * chooses the pass configuration for one series and length range --
  * lengths per pass (batch_lengths) and the batched form's speculation margin
  * (spec_scale), the select cap, the refine segment and the refine-form split
- * (direct_below, direct_below_long) and the refine strip height (refine_rows) -- by timing
+ * (direct_below, direct_below_long), the refine strip height (refine_rows) and the
+ * column chunks of the tensor-core direct refine (tc_chunks) -- by timing
  * candidates one setting at a time on blocks of up to 12 lengths at the
  * start, a third, two thirds and the end of [minL, maxL] of the caller's
  * series; every block after the first resumes from the schedule inputs of

@@ -111,7 +111,7 @@ struct palmad_ctx {
     // refine pool
     int32_t pool = 0;
     int32_t pool_kpad = 0, pool_nchunks = 0;
-    DBuf<int32_t> slot_lane, slot_win, route, dlist, dgroups, dead, kcnt, strip_row;
+    DBuf<int32_t> slot_lane, slot_win, route, dlist, dlist_alt, dgroups, dead, kcnt, strip_row;
     DBuf<float> topcen, topsum, seeds;
     DBuf<int4> seed_groups;
     bool sets_dirty = false;       // a pass stopped early: slot maps may not be clean
@@ -277,6 +277,9 @@ palmad_status read_options(palmad_ctx* ctx, const palmad_options* in, palmad_opt
     if (o.spec_scale < 0 || o.spec_scale > 400) return fail(ctx, PALMAD_ERR_ARG, "spec_scale must lie in [0, 400]");
     if (o.autotune != 0 && o.autotune != 1) return fail(ctx, PALMAD_ERR_ARG, "autotune must be 0 or 1");
     if (o.direct_below_long < 0) return fail(ctx, PALMAD_ERR_ARG, "direct_below_long must be >= 0");
+    if (o.tc_group != 0 && o.tc_group != 32 && o.tc_group != 64 && o.tc_group != 128 && o.tc_group != 256)
+        return fail(ctx, PALMAD_ERR_ARG, "tc_group must be 0, 32, 64, 128 or 256");
+    if (o.tc_chunks < 0 || o.tc_chunks > 64) return fail(ctx, PALMAD_ERR_ARG, "tc_chunks must lie in [0, 64]");
     if (o.refine_rows != 0 && o.refine_rows != kRefineH && o.refine_rows != kRefineHTall)
         return fail(ctx, PALMAD_ERR_ARG, "refine_rows must be 0, 128 or 256");
     return PALMAD_OK;
@@ -345,7 +348,8 @@ palmad_status ensure_pool(palmad_ctx* ctx, int32_t kpad, int32_t nchunks) {
     slots = std::min<int64_t>(slots, 1 << 17);
     slots = std::max<int64_t>(64, (slots / 64) * 64);
     CKS(ensure(ctx, ctx->slot_lane, slots)); CKS(ensure(ctx, ctx->slot_win, slots)); CKS(ensure(ctx, ctx->route, slots));
-    CKS(ensure(ctx, ctx->dlist, slots)); CKS(ensure(ctx, ctx->dgroups, slots / 64 + 1));
+    CKS(ensure(ctx, ctx->dlist, slots)); CKS(ensure(ctx, ctx->dlist_alt, slots));
+    CKS(ensure(ctx, ctx->dgroups, slots / 64 + 1));
     CKS(ensure(ctx, ctx->dead, slots)); CKS(ensure(ctx, ctx->kcnt, slots)); CKS(ensure(ctx, ctx->asum, slots)); CKS(ensure(ctx, ctx->gmax, slots));
     CKS(ensure(ctx, ctx->nn2, slots));
     CKS(ensure(ctx, ctx->acen, size_t(slots) * kpad));
@@ -373,6 +377,10 @@ Pass base_pass(palmad_ctx* ctx, int nl, int K, bool exclusive, const palmad_opti
     p.slot_win = ctx->slot_win.p;
     p.route = ctx->route.p;
     p.dlist = ctx->dlist.p;
+    p.dlist_alt = ctx->dlist_alt.p;
+    p.tc_ns = o.tc_group;
+    p.tc_col_lo = 0;
+    p.tc_col_hi = int64_t(1) << 40;  // every column
     p.dgroups = ctx->dgroups.p;
     p.acen = ctx->acen.p;
     p.asum = ctx->asum.p;
@@ -574,8 +582,26 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
         LAUNCH(PALMAD_K_PLAN, launch_plan(p, ctx->stream));
         if (p.tc_seeds) LAUNCH(PALMAD_K_SEED_TC, launch_seeds(p, ctx->sms, ctx->stream));
         LAUNCH(PALMAD_K_REFINE_SWEEP, launch_refine_sweep(p, ctx->sms * 4, ctx->stream));
-        if (p.mixed) LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_tc(p, ctx->sms, ctx->stream));
-        else LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_direct(p, ctx->sms * 2, ctx->stream));
+        if (p.mixed) {
+            // the tensor-core direct refine in column chunks; between chunks
+            // the survivors still alive are re-packed into full groups, so a
+            // group no longer runs on while most of its survivors are pruned
+            const int chunks = o.tc_chunks > 0 ? o.tc_chunks : 1;
+            const int64_t span = ((p.nmax + chunks - 1) / chunks + 2047) / 2048 * 2048;
+            for (int c = 0; c < chunks && int64_t(c) * span < p.nmax; ++c) {
+                p.tc_col_lo = int64_t(c) * span;
+                p.tc_col_hi = std::min<int64_t>(p.nmax, p.tc_col_lo + span);
+                if (c > 0) {
+                    CK(cudaMemsetAsync(&ctx->small.p->work[1], 0, sizeof(int32_t), ctx->stream));
+                    CK(cudaMemsetAsync(&ctx->small.p->work[4], 0, sizeof(int32_t), ctx->stream));
+                    LAUNCH(PALMAD_K_PLAN, launch_direct_repack(p, ctx->stream));
+                    std::swap(p.dlist, p.dlist_alt);
+                }
+                LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_tc(p, ctx->sms, ctx->stream));
+            }
+        } else {
+            LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_direct(p, ctx->sms * 2, ctx->stream));
+        }
         LAUNCH(PALMAD_K_RECHECK, launch_recheck(p, ctx->sms * 8, ctx->stream));
         if (io.mode == kRefine) LAUNCH(PALMAD_K_GATHER, launch_shard_out(p, ctx->stream));
         else LAUNCH(PALMAD_K_GATHER, launch_gather(p, ctx->stream));
@@ -598,6 +624,7 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
     if (sm.err) return fail(ctx, PALMAD_ERR_TIMEOUT, "tensor-core refine: an MMA did not signal completion");
     ctx->stats.select_pairs += int64_t(sm.pairs[0]);
     ctx->stats.refine_pairs += int64_t(sm.pairs[1]) + int64_t(sm.pairs[4]);
+    ctx->stats.direct_pairs += int64_t(sm.pairs[1]);
     ctx->stats.fp64_pairs += int64_t(sm.pairs[2]);
     // algorithmic work: per-lane m is folded with the pass-average m (exact for one length)
     double msum = 0.0;
@@ -1252,6 +1279,16 @@ palmad_status tune(palmad_ctx* ctx, const float* T_dev, int64_t n, int32_t minL,
             CKS(consider(o));
         }
     }
+    // column chunks of the tensor-core direct refine (live survivors re-packed
+    // between chunks)
+    if (cur.precision == PALMAD_PREC_MIXED) {
+        const palmad_options start = cur;
+        for (int32_t ch : {4, 8}) {
+            palmad_options o = start;
+            o.tc_chunks = ch;
+            CKS(consider(o));
+        }
+    }
     // rows per refine strip
     {
         const palmad_options start = cur;
@@ -1376,7 +1413,7 @@ void palmad_destroy(palmad_ctx* ctx) {
     release(ctx->lanes); release(ctx->st); release(ctx->chain); release(ctx->small);
     release(ctx->pidx); release(ctx->pnn);
     release(ctx->slot_lane); release(ctx->slot_win); release(ctx->route); release(ctx->dlist); release(ctx->dgroups); release(ctx->dead);
-    release(ctx->kcnt);
+    release(ctx->kcnt); release(ctx->dlist_alt);
     release(ctx->acen); release(ctx->asum); release(ctx->cmax); release(ctx->cmax2); release(ctx->gmax); release(ctx->nn2);
     release(ctx->strips); release(ctx->init_flags);
     release(ctx->strip_row); release(ctx->topcen); release(ctx->topsum); release(ctx->seeds); release(ctx->seed_groups);

@@ -145,17 +145,61 @@ __global__ void k_plan_split(const Pass p) {
     }
 }
 
-// Groups of 64 packed direct slots, listed so the direct refine visits only
-// groups that hold work (count in work[4]).
+// Groups of kDGroup packed direct slots, listed so the direct refine visits
+// only groups that hold work (count in work[4]).
 __global__ void k_plan_groups(const Pass p) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= p.nl) return;
     const int32_t nd = p.st[l].ndirect;
     if (nd <= 0) return;
-    const int32_t ng = (nd + 63) / 64;
+    const int32_t ng = (nd + kDGroup - 1) / kDGroup;
     const int32_t at = atomicAdd(p.work + 4, ng);
     const int32_t base = p.lanes[l].slot_base;
-    for (int32_t k = 0; k < ng; ++k) p.dgroups[at + k] = base + 64 * k;
+    for (int32_t k = 0; k < ng; ++k) p.dgroups[at + k] = base + kDGroup * k;
+}
+
+// Between the column chunks of the tensor-core direct refine: the lane's
+// direct survivors still alive, re-packed in order from dlist into dlist_alt
+// (one CTA per lane, prefix sum over the entries); ndirect becomes their
+// number, so the next chunk's groups hold live survivors only.
+__global__ void __launch_bounds__(1024) k_direct_compact(const Pass p) {
+    __shared__ int32_t warp_tot[32];
+    __shared__ int32_t total_s;
+    const int l = blockIdx.x;
+    const int32_t nd = p.st[l].ndirect;
+    const int32_t base = p.lanes[l].slot_base;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int32_t per = (nd + int32_t(blockDim.x) - 1) / int32_t(blockDim.x);
+    const int32_t q0 = min(nd, tid * per), q1 = min(nd, q0 + per);
+    int32_t cnt = 0;
+    for (int32_t q = q0; q < q1; ++q) cnt += __ldcg(&p.dead[p.dlist[base + q]]) ? 0 : 1;
+    int32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int32_t v = warp_tot[lane];
+        int32_t t = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t u = __shfl_up_sync(kFull, t, o);
+            if (lane >= o) t += u;
+        }
+        warp_tot[lane] = t - v;
+        if (lane == 31) total_s = t;
+    }
+    __syncthreads();
+    int32_t off = warp_tot[wid] + incl - cnt;
+    for (int32_t q = q0; q < q1; ++q) {
+        const int32_t g = p.dlist[base + q];
+        if (!__ldcg(&p.dead[g])) p.dlist_alt[base + off++] = g;
+    }
+    __syncthreads();  // every thread has read ndirect before it changes
+    if (tid == 0) p.st[l].ndirect = total_s;
 }
 
 // --------------------------------------------------------------- prep
@@ -197,7 +241,8 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t ngroups = *reinterpret_cast<volatile int32_t*>(p.work + 4);
     const int64_t ntiles = (p.nmax + kRC - 1) / kRC;
-    const int64_t nitems = ngroups * ntiles;
+    constexpr int64_t kSub = kDGroup / kRS;  // 64-survivor tiles per group
+    const int64_t nitems = ngroups * kSub * ntiles;
     unsigned long long pairs = 0;
 
     for (;;) {
@@ -208,9 +253,11 @@ __global__ void __launch_bounds__(256) k_refine(const Pass p) {
         __syncthreads();
         const int64_t item = item_s;
         if (item >= nitems) break;
-        const int64_t gbase = p.dgroups[item / ntiles];
+        const int64_t gsub = item / ntiles;
+        const int64_t g0 = p.dgroups[gsub / kSub];     // a slot of the group's lane
+        const int64_t gbase = g0 + (gsub % kSub) * kRS;
         const int32_t t = int32_t(item % ntiles);
-        const int l = p.slot_lane[gbase];
+        const int l = p.slot_lane[g0];
         const Lane& L = p.lanes[l];
         const int64_t N = L.N;
         const int64_t j0 = int64_t(t) * kRC;
@@ -532,6 +579,13 @@ cudaError_t launch_plan(const Pass& p, cudaStream_t s) {
     k_plan_groups<<<(p.nl + block - 1) / block, block, 0, s>>>(p);
     const int pgrid = int(min64((int64_t(p.nslots) * 32 + block - 1) / block, 4096));
     k_prep<<<pgrid, block, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direct_repack(const Pass& p, cudaStream_t s) {
+    if (p.nslots <= 0) return cudaSuccess;
+    k_direct_compact<<<p.nl, 1024, 0, s>>>(p);
+    k_plan_groups<<<(p.nl + 255) / 256, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

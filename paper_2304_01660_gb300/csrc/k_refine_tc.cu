@@ -72,7 +72,8 @@ __host__ __device__ inline TcLayout tc_layout(int kp, int ns, int tiles) {
     t.off_t = t.off_al + 2 * t.a_bytes;      // series slice (FP32)
     t.off_c = t.off_t + size_t(tc_span(kp, tiles)) * 4;  // column records (inv, mu)
     t.off_misc = t.off_c + size_t(tiles * kTcM) * 8;
-    // misc: survivor records (float4), slots, lower-bound maxima; mbar[2]; tmem slot; flag
+    // misc: survivor records (float4), slots, lower-bound maxima, coarse
+    // maxima; mbar[2]; tmem slot; flag
     t.total = t.off_misc + size_t(ns) * (16 + 4 + 4 + 8) + 64;
     return t;
 }
@@ -110,8 +111,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t idesc = instr_desc(kTcM, NS);
     const int64_t ngroups = *reinterpret_cast<volatile int32_t*>(p.work + 4);
-    const int64_t nhalf = 64 / NS;  // MMA groups per 64-slot direct group
-    const int64_t nblk = (p.nmax + kTcM * tiles_item - 1) / (kTcM * tiles_item);
+    const int64_t nhalf = kDGroup / NS;  // MMA groups per direct group
+    // the launch's column chunk [tc_col_lo, tc_col_hi), in work-item blocks
+    const int64_t iw = int64_t(kTcM) * tiles_item;
+    const int64_t blk0 = p.tc_col_lo / iw;
+    const int64_t nblk = max64(0, min64((p.tc_col_hi + iw - 1) / iw, (p.nmax + iw - 1) / iw) - blk0);
     const int64_t nitems = ngroups * nhalf * nblk;
 
     if (tid == 0) {
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
         const int64_t N = L.N, n = L.n;
         const int32_t m = L.m, kpad = L.kpad;
         const int32_t nd = min64(NS, int64_t(S.ndirect) - (gbase - L.slot_base));
-        const int64_t jstart = blk * int64_t(kTcM * tiles_item);
+        const int64_t jstart = (blk0 + blk) * iw;
         if (nd <= 0 || jstart >= N) {
             __syncthreads();
             continue;
@@ -261,9 +265,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_refine_tc(const Pass p) {
             const int32_t chunk = int32_t((j0 >> 5) + wq);
             const bool chunk_ok = t * kTcM + 32 * wq < nloc;  // chunks past the lane's last column are not stored
             const uint32_t excl = uint32_t(2 * m - 1);
-            // survivors 32 hs .. 32 hs + 31 (NS = 32: the second warpgroup idles)
-            const int h = hs;
-            if (32 * h < nd && h < NS / 32) {
+            // survivor sub-blocks hs, hs + 2, ... (32 survivors each)
+            for (int h = hs; h < NS / 32 && 32 * h < nd; h += 2) {
                 float v[32];
                 tmem_ld32(tmem + (uint32_t(32 * wq) << 16) + uint32_t(b * NS + 32 * h), v);
                 float keep = -kInf;
@@ -367,21 +370,27 @@ bool refine_tc_supported(const Pass& p) { return p.kpad_pass <= 1024 && p.nmax <
 
 cudaError_t launch_refine_tc(const Pass& p, int sms, cudaStream_t s) {
     if (p.nslots <= 0) return cudaSuccess;
-    const int ns = p.kpad_pass <= 512 ? 64 : 32;
+    // survivors per MMA (the MMA's N): 64, or 32 for windows above 512 (shared
+    // memory); 128 or 256 when asked (palmad_options.tc_group): each
+    // tcgen05.mma then carries more work for the one issuing thread, but a
+    // group runs until its last survivor is pruned
+    int ns = p.tc_ns > 0 ? p.tc_ns : (p.kpad_pass <= 512 ? 64 : 32);
+    while (ns > 32 && tc_layout(p.kpad_pass, ns, kTcTiles).total > size_t(227 * 1024)) ns /= 2;  // what fits
     const TcLayout lay = tc_layout(p.kpad_pass, ns, tc_tiles(p, ns));
-    // at least 76 KB per CTA: at most 2 CTAs (2 x 128 TMEM columns) per SM
+    // at least 76 KB per CTA: at most 2 CTAs (2 x 128 TMEM columns) per SM;
+    // NS = 128 and 256 take half or all of TMEM and run one CTA per SM
     const size_t smem = lay.total > 78 * 1024 ? lay.total : size_t(78 * 1024);
-    cudaError_t e;
-    if (ns == 64) {
-        e = cudaFuncSetAttribute(k_refine_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (smem > size_t(227 * 1024)) return cudaErrorInvalidValue;
+    auto go = [&](auto kern, int ctas) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        k_refine_tc<64><<<sms * 2, kTcThreads, smem, s>>>(p);
-    } else {
-        e = cudaFuncSetAttribute(k_refine_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-        k_refine_tc<32><<<sms * 2, kTcThreads, smem, s>>>(p);
-    }
-    return cudaGetLastError();
+        kern<<<sms * ctas, kTcThreads, smem, s>>>(p);
+        return cudaGetLastError();
+    };
+    if (ns == 256) return go(k_refine_tc<256>, 1);
+    if (ns == 128) return go(k_refine_tc<128>, 1);
+    if (ns == 64) return go(k_refine_tc<64>, 2);
+    return go(k_refine_tc<32>, 2);
 }
 
 }  // namespace palmad

@@ -27,6 +27,7 @@ constexpr int kCoarseMin = 1024;  // smallest coarse block of the chunk maxima (
 constexpr int kSelPieceCols = 512;       // columns per select work item (a strip's scan is cut into pieces)
 constexpr int kSelPieceColsShort = 256;  // the same for passes with too few strips to fill the GPU
 constexpr int kMaxK = 1024;    // largest top-K
+constexpr int kDGroup = 256;   // direct-form survivors per group (packed per lane; the direct kernels split them)
 constexpr int kMaxKnn = 16;    // largest k of the k-th neighbour variant
 
 // Per-window data the FP32 kernels read, one 16-byte record per window:
@@ -139,7 +140,7 @@ struct Pass {
     int32_t* slot_win;     // [slots] window of each slot, -1 for padding
     int32_t* route;        // [slots] 0 sweep, 1 direct, -1 none
     int32_t* dlist;        // [slots] direct-form slots of each lane, packed from its slot_base
-    int32_t* dgroups;      // [slots/64] first dlist entry of every 64-entry group holding direct slots
+    int32_t* dgroups;      // [slots/64] first dlist entry of every kDGroup-entry group holding direct slots
     float* acen;           // [slots][kpad_max] centred survivor windows
     float* asum;           // [slots]
     uint32_t* gmax;        // [slots] enc_f32 of the maximum rho
@@ -166,7 +167,9 @@ struct Pass {
     int4* seed_groups;     // (lane, first row, rows, -) per group of <= 32 rows of one lane
     int32_t* seed_ngroups;
     int32_t sharded;       // 1: a lane restricts its columns (k_prep clears every coarse maximum)
-    int32_t pad7;
+    int32_t tc_ns;         // survivors per tensor-core MMA (0: 64, or 32 for windows above 512)
+    int32_t* dlist_alt;    // [slots] second packed direct list (alive survivors re-packed between column chunks)
+    int64_t tc_col_lo, tc_col_hi;  // the tensor-core direct refine's columns this launch (multiples of 2048)
     double* shard_nn;      // [N of lane 0] per-candidate result of a refine shard, or nullptr
     int32_t* err;          // set to 1 by a kernel whose bounded wait gave up
     int32_t* work;         // [8] work counters, zeroed per launch group
@@ -227,6 +230,7 @@ bool refine_tc_supported(const Pass& p);
 bool seed_tc_supported(const Pass& p);
 cudaError_t launch_seeds(const Pass& p, int sms, cudaStream_t s);
 cudaError_t launch_refine_tc(const Pass& p, int sms, cudaStream_t s);
+cudaError_t launch_direct_repack(const Pass& p, cudaStream_t s);
 cudaError_t launch_recheck(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_round_cleanup(const Pass& p, cudaStream_t s);
 cudaError_t launch_shard_out(const Pass& p, cudaStream_t s);

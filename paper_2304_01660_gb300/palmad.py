@@ -51,6 +51,8 @@ class Options(ctypes.Structure):
         ("autotune", ctypes.c_int32),
         ("refine_rows", ctypes.c_int32),
         ("direct_below_long", ctypes.c_int32),
+        ("tc_group", ctypes.c_int32),
+        ("tc_chunks", ctypes.c_int32),
     ]
 
 
@@ -79,6 +81,7 @@ class Stats(ctypes.Structure):
         ("refine_strips", ctypes.c_int64),
         ("sweep_survivors", ctypes.c_int64),
         ("tune_ms", ctypes.c_double),
+        ("direct_pairs", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -101,7 +104,7 @@ class TuneReport(ctypes.Structure):
 
 
 TUNED_FIELDS = ("batch_lengths", "spec_scale", "select_cap", "refine_seg", "direct_below", "direct_below_long",
-                "refine_rows")
+                "refine_rows", "tc_chunks")
 
 _lib = None
 _vp = ctypes.c_void_p

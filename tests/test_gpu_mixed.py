@@ -42,6 +42,29 @@ def test_mixed_drag_long_windows(ctx, m):
     _check_drag(ctx, T, m, 0.0, _opts(**ALL_TC))
 
 
+@pytest.mark.parametrize("group", [0, 128, 256])
+@pytest.mark.parametrize("name", list(SERIES))
+def test_mixed_chunks_and_groups_match_oracle(ctx, name, group):
+    """The direct refine in column chunks, live survivors re-packed between
+    chunks, with 64 / 128 / 256 survivors per MMA (256 only fits windows up to
+    128, so m = 200 falls back to 128)."""
+    T = SERIES[name]()
+    for m in (8, 100, 200):
+        mp, _ = oracle.matrix_profile(T, m)
+        for r in _thresholds(mp, (0.5, 0.99, 1.0)):
+            _check_drag(ctx, T, m, float(r), _opts(**ALL_TC, tc_chunks=4, tc_group=group))
+
+
+@pytest.mark.parametrize("chunks", [3, 8])
+def test_mixed_chunked_merlin_matches_oracle(ctx, chunks):
+    """A 20 000-point series spans several 2048-column chunks."""
+    T = synth.random_walk(20000, 62)
+    got = ctx.palmad_find_discords(T, 40, 60, 2, _opts(precision=MIXED, direct_below=16, tc_chunks=chunks,
+                                                        batch_lengths=4), heatmap=True)
+    want = oracle.merlin(T, 40, 60, 2, True, heatmap=True)
+    _check_merlin(got, want, heat=True)
+
+
 def test_mixed_drag_degenerate_thresholds(ctx):
     T = SERIES["rw3000"]()
     m = 20
