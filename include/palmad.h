@@ -143,6 +143,11 @@ typedef struct {
     int32_t tc_chunks;       /* mixed precision: the direct refine of a round runs over the
                                 columns in this many chunks (0 = 1), re-packing the
                                 survivors still alive into full groups between chunks */
+    int32_t tc_form;         /* mixed precision, tensor-core direct refine: 0 (default)
+                                survivor-major where the windows allow it (up to 256 points:
+                                128 survivors per MMA, 256 columns per tile, warp-specialised),
+                                column-major otherwise; 1 column-major always; 2 survivor-
+                                major where the windows allow it.  Results are the same */
 } palmad_options;
 
 /* Per-call counters of the most recent find/drag call. */

@@ -280,6 +280,7 @@ palmad_status read_options(palmad_ctx* ctx, const palmad_options* in, palmad_opt
     if (o.tc_group != 0 && o.tc_group != 32 && o.tc_group != 64 && o.tc_group != 128 && o.tc_group != 256)
         return fail(ctx, PALMAD_ERR_ARG, "tc_group must be 0, 32, 64, 128 or 256");
     if (o.tc_chunks < 0 || o.tc_chunks > 64) return fail(ctx, PALMAD_ERR_ARG, "tc_chunks must lie in [0, 64]");
+    if (o.tc_form < 0 || o.tc_form > 2) return fail(ctx, PALMAD_ERR_ARG, "tc_form must be 0, 1 or 2");
     if (o.refine_rows != 0 && o.refine_rows != kRefineH && o.refine_rows != kRefineHTall)
         return fail(ctx, PALMAD_ERR_ARG, "refine_rows must be 0, 128 or 256");
     return PALMAD_OK;
@@ -587,6 +588,8 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
             // the survivors still alive are re-packed into full groups, so a
             // group no longer runs on while most of its survivors are pruned
             const int chunks = o.tc_chunks > 0 ? o.tc_chunks : 1;
+            // survivor-major tiles (windows up to 256) unless asked otherwise
+            const bool tcs = o.tc_form != 1 && p.tc_ns == 0 && refine_tcs_supported(p);
             const int64_t span = ((p.nmax + chunks - 1) / chunks + 2047) / 2048 * 2048;
             for (int c = 0; c < chunks && int64_t(c) * span < p.nmax; ++c) {
                 p.tc_col_lo = int64_t(c) * span;
@@ -597,7 +600,8 @@ palmad_status run_pass(palmad_ctx* ctx, std::vector<PassLane>& req, int K, bool 
                     LAUNCH(PALMAD_K_PLAN, launch_direct_repack(p, ctx->stream));
                     std::swap(p.dlist, p.dlist_alt);
                 }
-                LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_tc(p, ctx->sms, ctx->stream));
+                if (tcs) LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_tcs(p, ctx->sms, ctx->stream));
+                else LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_tc(p, ctx->sms, ctx->stream));
             }
         } else {
             LAUNCH(PALMAD_K_REFINE_DIRECT, launch_refine_direct(p, ctx->sms * 2, ctx->stream));

@@ -230,6 +230,8 @@ bool refine_tc_supported(const Pass& p);
 bool seed_tc_supported(const Pass& p);
 cudaError_t launch_seeds(const Pass& p, int sms, cudaStream_t s);
 cudaError_t launch_refine_tc(const Pass& p, int sms, cudaStream_t s);
+bool refine_tcs_supported(const Pass& p);
+cudaError_t launch_refine_tcs(const Pass& p, int sms, cudaStream_t s);
 cudaError_t launch_direct_repack(const Pass& p, cudaStream_t s);
 cudaError_t launch_recheck(const Pass& p, int grid, cudaStream_t s);
 cudaError_t launch_round_cleanup(const Pass& p, cudaStream_t s);

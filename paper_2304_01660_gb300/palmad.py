@@ -53,6 +53,7 @@ class Options(ctypes.Structure):
         ("direct_below_long", ctypes.c_int32),
         ("tc_group", ctypes.c_int32),
         ("tc_chunks", ctypes.c_int32),
+        ("tc_form", ctypes.c_int32),
     ]
 
 

@@ -23,13 +23,45 @@ ALL_TC = dict(precision=MIXED, direct_below=129)
 ALL_SEED = dict(precision=MIXED, tc_seed_min=1)   # every swept strip seeded on the tensor cores
 
 
+@pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("name", list(SERIES))
-@pytest.mark.parametrize("m", [8, 37, 100])
-def test_mixed_drag_matches_oracle(ctx, name, m):
+@pytest.mark.parametrize("m", [8, 37, 100, 256])
+def test_mixed_drag_matches_oracle(ctx, name, m, form):
+    """form 0: survivor-major tiles (windows up to 256); 1: column-major."""
     T = SERIES[name]()
     mp, _ = oracle.matrix_profile(T, m)
     for r in _thresholds(mp, (0.5, 0.9, 0.99, 1.0)):
-        _check_drag(ctx, T, m, float(r), _opts(**ALL_TC))
+        _check_drag(ctx, T, m, float(r), _opts(**ALL_TC, tc_form=form))
+
+
+_MANY = {}
+
+
+def _many_groups_case(m):
+    """40 000-point random walk and a threshold near the 95th percentile of
+    sampled nearest-neighbour distances (midway between two sampled values),
+    with the oracle's range discords (cached per m)."""
+    if m not in _MANY:
+        T = synth.random_walk(40000, 63)
+        N = len(T) - m + 1
+        idx = np.random.default_rng(m).choice(N, size=200, replace=False)
+        d = np.sort([oracle.nn_one(T, m, int(i))[0] for i in idx])
+        r = float(0.5 * (d[189] + d[190]))
+        _MANY[m] = (T, r, oracle.drag(T, m, r))
+    return _MANY[m]
+
+
+@pytest.mark.parametrize("chunks", [0, 3])
+@pytest.mark.parametrize("m", [64, 200])
+def test_mixed_survivor_major_many_groups(ctx, m, chunks):
+    """Thousands of direct survivors (several 256-survivor groups, two MMA
+    halves each), five 8192-column work items per group, a ragged last tile,
+    and column chunks that do not align with the work items."""
+    T, r, (wi, wn) = _many_groups_case(m)
+    assert len(wi) > 512
+    gi, gn = ctx.palmad_drag(T, m, r, _opts(**ALL_TC, tc_form=2, tc_chunks=chunks))
+    np.testing.assert_array_equal(gi, wi)
+    np.testing.assert_allclose(gn, wn, rtol=NN_RTOL, atol=0)
 
 
 @pytest.mark.parametrize("m", [520, 600])
