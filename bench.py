@@ -412,7 +412,7 @@ def run_ours(args, w):
         launches_per = dict(last_stats["launches"])
         tensor = dom == "refine_direct" and tuned.precision == 1
         src = {"refine_sweep": "paper_2304_01660_gb300/csrc/k_sweep.cu",
-               "refine_direct": "paper_2304_01660_gb300/csrc/k_refine_tc.cu" if tensor
+               "refine_direct": "paper_2304_01660_gb300/csrc/k_refine_tcs.cu" if tensor
                else "paper_2304_01660_gb300/csrc/k_refine.cu"}.get(dom, "")
         trf = TRAFFIC.get(dom if not tensor else "refine_direct_tc")
         traffic = None
@@ -425,7 +425,8 @@ def run_ours(args, w):
                 # a contraction on the tensor cores: the measured bf16 dense peak,
                 # sustained (the kernel runs inside a seconds-long step)
                 tpk = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
-                roof = {"kernel": "refine_direct (tcgen05, k_refine_tc)", "bound": "tensor", "achieved": ach,
+                roof = {"kernel": "refine_direct (tcgen05: k_refine_tcs, survivor-major, windows up to 256; "
+                                  "k_refine_tc, column-major, longer windows)", "bound": "tensor", "achieved": ach,
                         "peak": tpk, "unit": "TFLOP/s", "frac": ach / tpk if tpk else None, "traffic": traffic,
                         "traffic_unit": "bytes per launch",
                         "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, of measured)",

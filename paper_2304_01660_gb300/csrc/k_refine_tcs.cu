@@ -33,14 +33,21 @@
 // shared abort flag, every role leaves its tile loop, and the CTA reports the
 // error through p.err.
 //
-// Numerics are those of k_refine_tc.cu: the same split, the same number of
+// Numerics follow k_refine_tc.cu: the same split, the same number of
 // accumulating MMAs (3 kpad / 16), b0 the FP32 mean of the tile's middle
-// column, and the same per-column bound eps_j; the epilogue applies 1/sigma_j
-// per column and 1/sigma_g after the chunk maximum (both positive, so the
-// maximum commutes), and the lane's FP32 bound covers those roundings as it
-// covers the column-major epilogue's.  A survivor is pruned only when
-// rho - eps exceeds the lane's pruning threshold; chunk maxima hold upper
-// bounds and the survivor maximum a lower bound for the FP64 re-check.
+// column.  The epilogue takes rho(g, j) = D[g][j] / (sqrt(m) sigma_j) /
+// (sqrt(m) sigma_g), without the centring correction (mu_j - b0) sum_k a_g[k]
+// of the column-major kernel: a_g is centred, so its FP32 sum is a few
+// roundings of the window, and the bound takes the dropped term instead,
+//     eps_j = eps_j(column-major) + |mu_j - b0| / (sqrt(m) sigma_j) * S,
+//     S = max over the item's survivors of |sum_k a_g[k]| / (sqrt(m) sigma_g),
+// so a column needs one FP32 record (1 / (sqrt(m) sigma_j)) and one multiply
+// per survivor.  1/sigma_j is applied per column and 1/sigma_g after the
+// chunk maximum (both positive, so the maximum commutes), and the lane's
+// FP32 bound covers those roundings as it covers the column-major
+// epilogue's.  A survivor is pruned only when rho - eps exceeds the lane's
+// pruning threshold; chunk maxima hold upper bounds and the survivor maximum
+// a lower bound for the FP64 re-check.
 #include "tc_util.cuh"
 
 namespace palmad {
@@ -61,7 +68,7 @@ struct TcsLayout {
     int kp, stages;
     size_t a_bytes;     // one split of the survivor operand
     size_t h_bytes;     // one split of a tile's Hankel copies
-    size_t slot_bytes;  // bh, bl, column records, chunk bounds
+    size_t slot_bytes;  // bh, bl, column factors 1 / (sqrt(m) sigma_j), chunk bounds
     size_t off_ah, off_al, off_ring, off_bar, total;
 };
 
@@ -71,16 +78,16 @@ __host__ __device__ inline TcsLayout tcs_layout(int kp, int stages) {
     t.stages = stages;
     t.a_bytes = size_t(kSM) * kp * 2;
     t.h_bytes = size_t(kSN / 8 + kp / 8) * 128;
-    t.slot_bytes = 2 * t.h_bytes + size_t(kSN) * 8 + 64;
+    t.slot_bytes = 2 * t.h_bytes + size_t(kSN) * 4 + 64;
     t.slot_bytes = (t.slot_bytes + 127) / 128 * 128;
     t.off_ah = 0;
     t.off_al = t.a_bytes;
     t.off_ring = 2 * t.a_bytes;
     t.off_bar = t.off_ring + size_t(stages) * t.slot_bytes;
     // barriers: full, empty, cfree per stage; accfull, accempty per
-    // accumulator; then the item, the TMEM slot, the abort and alive flags
-    // and the item's survivor slots
-    t.total = t.off_bar + size_t(3 * stages + 4) * 8 + 32 + size_t(kSM) * 4;
+    // accumulator; then the item, the TMEM slot, the abort and alive flags,
+    // the item's survivor slots and the partial maxima of S
+    t.total = t.off_bar + size_t(3 * stages + 4) * 8 + 32 + size_t(kSM) * 4 + 16;
     return t;
 }
 
@@ -95,6 +102,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(smem_u32(b)) : "memory");
+}
+
+// max(a, b, c) in one instruction (three-input max.f32).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 // One lane of the warp polls (bounded), the warp learns the outcome; a
@@ -127,6 +141,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
     volatile int* s_alive = s_abort + 1;
     int32_t* s_slot = const_cast<int32_t*>(reinterpret_cast<volatile int32_t*>(s_alive + 1));  // [kSM]
+    float* s_smax = reinterpret_cast<float*>(s_slot + kSM);  // [4] S of the survivors of warps 4-7
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -200,6 +215,11 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
                 if (warp < 8) s_slot[s] = g;
             } else if (warp < 8) {
                 s_slot[s] = -1;
+            }
+            if (warp < 8) {
+                // S of the item: the largest |sum_k a_g[k]| / (sqrt(m) sigma_g)
+                const float sg = warp_max(g >= 0 ? fabsf(suma) * inv_s : 0.f);
+                if (lane == 0) s_smax[warp - 4] = sg;
             }
         }
         __syncthreads();
@@ -278,6 +298,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
                                         float(3 * kpad / 16 + 1) * 1.1920928955078125e-07f);
             const float* T = L.T;
             const int64_t n = L.n;
+            const float smax = 1.01f * fmaxf(fmaxf(s_smax[0], s_smax[1]), fmaxf(s_smax[2], s_smax[3]));
             for (int t = 0; t < ntiles; ++t) {
                 const uint32_t u = gt + uint32_t(t);
                 const int sl = int(u % uint32_t(S));
@@ -287,24 +308,25 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
                 unsigned char* slot = smem + lay.off_ring + size_t(sl) * lay.slot_bytes;
                 unsigned char* bh = slot;
                 unsigned char* bl = slot + lay.h_bytes;
-                float2* crec = reinterpret_cast<float2*>(slot + 2 * lay.h_bytes);
-                float* ceps = reinterpret_cast<float*>(crec + kSN);
+                float* cinv = reinterpret_cast<float*>(slot + 2 * lay.h_bytes);
+                float* ceps = cinv + kSN;
                 const int64_t j0 = jstart + int64_t(t) * kSN;
                 const float b0 = L.win[min64(j0 + kSN / 2, L.N - 1)].w;
-                // columns 32 c + lane of the tile: (1 / (sqrt(m) sigma_j), mu_j - b0)
-                // and the largest eps_j of each 32-column chunk
+                // columns 32 c + lane of the tile: 1 / (sqrt(m) sigma_j) and the
+                // largest eps_j of each 32-column chunk
                 for (int c = pw; c < kSN / 32; c += kSProd) {
                     const int64_t j = j0 + 32 * c + lane;
-                    float inv = 0.f, dmu = 0.f, eps = 0.f;
+                    float inv = 0.f, eps = 0.f;
                     if (j < jend) {
                         const float4 w = __ldg(L.win + j);
                         inv = w.z;
-                        dmu = w.w - b0;
+                        const float dmu = w.w - b0;
                         const float tt = dmu * inv * sqrt_m;
-                        eps = inv > 0.f ? 2.f * cmul * sqrtf(fmaf(tt, tt, 1.f)) * 1.000001f + 2.384185791015625e-07f
+                        eps = inv > 0.f ? 2.f * cmul * sqrtf(fmaf(tt, tt, 1.f)) * 1.000001f + 2.384185791015625e-07f +
+                                              fabsf(dmu * inv) * 1.01f * smax
                                         : 0.f;
                     }
-                    crec[32 * c + lane] = make_float2(inv, dmu);
+                    cinv[32 * c + lane] = inv;
                     const float em = warp_max(eps);
                     if (lane == 0) ceps[c] = em;
                 }
@@ -350,8 +372,8 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
                 if (!warp_wait(&full[sl], ph, s_abort)) break;
                 fence_after();
                 const unsigned char* slot = smem + lay.off_ring + size_t(sl) * lay.slot_bytes;
-                const float2* crec = reinterpret_cast<const float2*>(slot + 2 * lay.h_bytes);
-                const float* ceps = reinterpret_cast<const float*>(crec + kSN);
+                const float* cinv = reinterpret_cast<const float*>(slot + 2 * lay.h_bytes);
+                const float* ceps = cinv + kSN;
                 const int64_t j0 = jstart + int64_t(t) * kSN;
                 const int64_t cb = j0 / p.seg;  // a tile lies in one coarse block
                 if (cb != cb_cur) {
@@ -373,27 +395,27 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
                     }
                     const int cl = 128 * hf + 32 * c4;  // first column of the chunk in the tile
                     const int64_t cj = j0 + cl;
-                    const float4* r4 = reinterpret_cast<const float4*>(crec + cl);
+                    const float4* i4 = reinterpret_cast<const float4*>(cinv + cl);
                     float mx = -kInf;
                     if (cj + 31 < jend && (cj > zhi || cj + 31 < zlo)) {
                         // no column of the chunk is excluded or past the last window
 #pragma unroll
-                        for (int c = 0; c < 32; c += 2) {
-                            const float4 rr = r4[c >> 1];
-                            mx = fmaxf(mx, fmaf(-rr.y, suma, v[c]) * rr.x);
-                            mx = fmaxf(mx, fmaf(-rr.w, suma, v[c + 1]) * rr.z);
+                        for (int c = 0; c < 32; c += 4) {
+                            const float4 iv = i4[c >> 2];
+                            mx = fmax3(mx, v[c] * iv.x, v[c + 1] * iv.y);
+                            mx = fmax3(mx, v[c + 2] * iv.z, v[c + 3] * iv.w);
                         }
                     } else {
 #pragma unroll
-                        for (int c = 0; c < 32; c += 2) {
-                            const float4 rr = r4[c >> 1];
-                            const int64_t j = cj + c;
-                            const bool ok0 = j < jend && uint32_t(int32_t(j) - zs) >= excl;
-                            const bool ok1 = j + 1 < jend && uint32_t(int32_t(j + 1) - zs) >= excl;
-                            const float v0 = fmaf(-rr.y, suma, v[c]) * rr.x;
-                            const float v1 = fmaf(-rr.w, suma, v[c + 1]) * rr.z;
-                            mx = ok0 ? fmaxf(mx, v0) : mx;
-                            mx = ok1 ? fmaxf(mx, v1) : mx;
+                        for (int c = 0; c < 32; c += 4) {
+                            const float4 iv = i4[c >> 2];
+                            const float x[4] = {v[c] * iv.x, v[c + 1] * iv.y, v[c + 2] * iv.z, v[c + 3] * iv.w};
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int64_t j = cj + c + q;
+                                const bool ok = j < jend && uint32_t(int32_t(j) - zs) >= excl;
+                                mx = ok ? fmaxf(mx, x[q]) : mx;
+                            }
                         }
                     }
                     // 1 / sigma_g >= 0 commutes with the maximum (a flat survivor: rho = 0)

@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, D <= 4 ? 4 : 3) k_sweep(con
         const LaneView a{Lg.T, Lg.n, Lg.N, Lg.m, Lg.win};
         const int32_t m = a.m;
         const int64_t N = a.N;
-        const int kp = ((m + 127) / 128) * 128;
+        const int kp = ((m + 31) / 32) * 32;  // top-row seed loop: 32 values of k per step
         const float rho_prune = rho_prune_of(Lg, p.st[l]);
         // [ja, jb): columns of this item; jt: first column right of the
         // exclusion zone of the top row (select's triangle starts there)
