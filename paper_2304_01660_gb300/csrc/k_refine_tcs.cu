@@ -19,12 +19,15 @@
 // The CTA (one per SM, all 512 TMEM columns) is warp-specialised:
 //   warp 0       one lane issues the MMAs of a tile into one of two TMEM
 //                accumulators (256 columns each) and commits them;
-//   warps 1-3    producers: for every tile, the column records
-//                (1/(sqrt(m) sigma_j), mu_j - b0, the chunk error bounds) and
-//                the split Hankel copies of the series slice into a ring slot;
-//   warps 4-11   epilogue: warp w reads TMEM lane quarter w % 4 and column
-//                half (w - 4) / 4 of the finished accumulator, releases it,
+//   warps 1-7    producers: for every tile, the column factors
+//                1/(sqrt(m) sigma_j), the chunk error bounds and the split
+//                Hankel copies of the series slice into a ring slot (up to
+//                6 slots);
+//   warps 8-15   epilogue: warp w reads TMEM lane quarter w % 4 and column
+//                half (w - 8) / 4 of the finished accumulator, releases it,
 //                and reduces 32-column chunks.
+// Seven producer warps keep the ring ahead of the MMAs (with three, the MMA
+// warp waited on them for about a quarter of its time).
 // Ring slots and accumulators are handed over with mbarriers (full / empty
 // per slot, a second release per slot for the column records the epilogue
 // reads, full / empty per accumulator).  The survivor operand is staged by
@@ -58,11 +61,13 @@ using namespace tc;
 
 constexpr int kSM = 128;          // survivors per MMA (M, TMEM lanes)
 constexpr int kSN = 256;          // columns per tile (N)
-constexpr int kSThreads = 384;    // 12 warps: MMA, 3 producers, 8 epilogue
-constexpr int kSProd = 3;         // producer warps
+constexpr int kSProd = 7;                     // producer warps (warps 1 .. kSProd)
+constexpr int kSEpi0 = kSProd + 1;            // first of the 8 epilogue warps
+constexpr int kSThreads = 32 * (kSEpi0 + 8);  // MMA warp, producers, epilogue
+static_assert(kSEpi0 % 4 == 0, "epilogue warp w reads TMEM lane quarter w % 4");
 constexpr int kSKpadMax = 256;    // the survivor operand of longer windows does not fit
 constexpr int kSTilesItem = 32;   // tiles per work item (8192 columns)
-constexpr int kSMaxStages = 4;
+constexpr int kSMaxStages = 6;
 
 struct TcsLayout {
     int kp, stages;
@@ -141,7 +146,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
     volatile int* s_alive = s_abort + 1;
     int32_t* s_slot = const_cast<int32_t*>(reinterpret_cast<volatile int32_t*>(s_alive + 1));  // [kSM]
-    float* s_smax = reinterpret_cast<float*>(s_slot + kSM);  // [4] S of the survivors of warps 4-7
+    float* s_smax = reinterpret_cast<float*>(s_slot + kSM);  // [4] S of the first four epilogue warps' survivors
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
         int32_t g = -1, zs = 0;
         float inv_s = 0.f, suma = 0.f;
         bool mine = false;
-        if (warp >= 4) {
+        if (warp >= kSEpi0) {
             const int s = 32 * (warp & 3) + lane;
             if (s < nd) {
                 g = p.dlist[gbase + s];
@@ -212,14 +217,14 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
                 zs = w - m + 1;  // columns zs .. zs + 2m - 2 overlap the survivor
                 mine = !__ldcg(&p.dead[g]);
                 if (mine) *s_alive = 1;
-                if (warp < 8) s_slot[s] = g;
-            } else if (warp < 8) {
+                if (warp < kSEpi0 + 4) s_slot[s] = g;
+            } else if (warp < kSEpi0 + 4) {
                 s_slot[s] = -1;
             }
-            if (warp < 8) {
+            if (warp < kSEpi0 + 4) {
                 // S of the item: the largest |sum_k a_g[k]| / (sqrt(m) sigma_g)
                 const float sg = warp_max(g >= 0 ? fabsf(suma) * inv_s : 0.f);
-                if (lane == 0) s_smax[warp - 4] = sg;
+                if (lane == 0) s_smax[warp - kSEpi0] = sg;
             }
         }
         __syncthreads();
@@ -352,8 +357,8 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
                 if (lane == 0) mbar_arrive(&full[sl]);
             }
         } else {
-            // ---- epilogue: survivor 32 (warp % 4) + lane, column half (warp - 4) / 4
-            const int q4 = warp & 3, hf = (warp - 4) >> 2;
+            // ---- epilogue: survivor 32 (warp % 4) + lane, column half (warp - kSEpi0) / 4
+            const int q4 = warp & 3, hf = (warp - kSEpi0) >> 2;
             const float rp = rho_prune_of(L, St);
             const uint32_t excl = uint32_t(2 * m - 1);
             const int64_t zlo = zs, zhi = int64_t(zs) + 2 * m - 2;
@@ -381,7 +386,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
                     c2run = 0u;
                     cb_cur = cb;
                 }
-                if (warp == 4 && lane == 0) pairs += uint64_t(nd) * uint64_t(min64(kSN, jend - j0));
+                if (warp == kSEpi0 && lane == 0) pairs += uint64_t(nd) * uint64_t(min64(kSN, jend - j0));
 #pragma unroll 1
                 for (int c4 = 0; c4 < 4; ++c4) {
                     float v[32];
@@ -457,7 +462,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_refine_tcs(const Pass p) {
     fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kSN) : "memory");
-    if (warp == 4 && lane == 0 && pairs) atomicAdd(p.pairs + 1, pairs);
+    if (warp == kSEpi0 && lane == 0 && pairs) atomicAdd(p.pairs + 1, pairs);
 }
 
 }  // namespace
