@@ -50,7 +50,11 @@ FIXTURE = os.path.join(ROOT, "tests", "golden", "beats1m_windows.json")
 # capture of a bounded case of this workload: (sha256[:16] of the kernel's
 # source file at the capture, bytes per pair).  The bench scales it to its own launches by their pair
 # counts; a source that no longer matches reports null.
-TRAFFIC: dict[str, tuple[str, float]] = {}
+# k_refine_tcs: beats1m m = 150..157, one launch of 54 684 tiles of 128 x 256
+# survivor-column pairs, 37.6 MB read + 159.4 MB written (the chunk maxima).
+TRAFFIC: dict[str, tuple[str, float]] = {
+    "refine_direct_tc": ("02d557a4a8607e7f", 197.0e6 / (54684 * 128 * 256)),
+}
 
 
 def _peaks():

@@ -1305,7 +1305,7 @@ palmad_status tune(palmad_ctx* ctx, const float* T_dev, int64_t n, int32_t minL,
     // touch disjoint passes, so each is searched on its own)
     {
         const palmad_options start = cur;
-        for (int32_t db : {2, 4, 8, 16, 32}) {
+        for (int32_t db : {2, 4, 8, 16, 32, 64, 129}) {
             palmad_options o = start;
             o.direct_below = db;
             o.direct_below_long = start.direct_below_long > 0 ? start.direct_below_long : start.direct_below;
