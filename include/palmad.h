@@ -243,7 +243,10 @@ const char *palmad_last_error(const palmad_ctx *ctx);
  *   out_r       [L] or NULL: the final r of each length.
  *   out_heatmap [L * (n - minL + 1)] float32 or NULL: row l = length
  *               minL + l holds nnDist^2 / (2m) at every range discord of
- *               that length and 0 elsewhere (Eq. 10).
+ *               that length and 0 elsewhere (Eq. 10).  It is computed in a
+ *               device buffer of the same size that the context keeps for
+ *               later calls (freed by palmad_destroy); pinned host memory
+ *               makes the copy out fastest.
  */
 palmad_status palmad_find_discords(palmad_ctx *ctx, const float *T, int64_t n, int32_t minL, int32_t maxL,
                                    int32_t topK, const palmad_options *opt, int64_t *out_idx,

@@ -85,6 +85,8 @@ struct palmad_ctx {
     int sms = 0;
 
     DBuf<float> T;                 // staged series (host entry points)
+    DBuf<float> heat_stage;        // device heatmap of the host entry points (kept: grown on demand)
+    DBuf<int64_t> count_stage;     // per-length range-discord counts of the host entry points
     DBuf<int32_t> hints;           // witness hints of the call's series (one int per point)
     std::vector<LaneSet> sets;
     // pass
@@ -1411,7 +1413,7 @@ void palmad_destroy(palmad_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    release(ctx->T);
+    release(ctx->T); release(ctx->heat_stage); release(ctx->count_stage);
     release(ctx->hints);
     for (LaneSet& s : ctx->sets) release_set(s);
     release(ctx->lanes); release(ctx->st); release(ctx->chain); release(ctx->small);
@@ -1512,16 +1514,13 @@ static palmad_status find_one(palmad_ctx* ctx, const float* T, int64_t n, int32_
     CKS(ensure(ctx, ctx->T, size_t(n)));
     CK(cudaMemcpyAsync(ctx->T.p, T, size_t(n) * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     if (minL_sched == minL) CKS(tuned_options(ctx, ctx->T.p, n, minL, maxL, topK, o));
-    DBuf<int64_t> cnt;
-    DBuf<float> heat;
+    // the counts and the heatmap are staged in context buffers kept between
+    // calls, so repeated calls do not allocate and free a heatmap that is
+    // gigabytes for a long series
+    DBuf<int64_t>& cnt = ctx->count_stage;
+    DBuf<float>& heat = ctx->heat_stage;
     CKS(ensure(ctx, cnt, L));
-    if (out_heatmap) {
-        palmad_status a = ensure(ctx, heat, size_t(L) * hw);
-        if (a != PALMAD_OK) {
-            release(cnt);
-            return a;
-        }
-    }
+    if (out_heatmap) CKS(ensure(ctx, heat, size_t(L) * hw));
     std::vector<SeriesJob> jobs(1);
     SeriesJob& s = jobs[0];
     s.T = ctx->T.p;
@@ -1555,8 +1554,6 @@ static palmad_status find_one(palmad_ctx* ctx, const float* T, int64_t n, int32_
         if (out_r) std::memcpy(out_r, s.r_final.data(), L * sizeof(double));
         count_discords(ctx, counts);
     }
-    release(cnt);
-    release(heat);
     return st;
 }
 
