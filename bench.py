@@ -274,6 +274,7 @@ def run_ours(args, w):
     import torch
     import torch.distributed as dist
     from paper_2304_01660_gb300 import _build, palmad
+    from paper_2304_01660_gb300 import dist as pdist
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -356,11 +357,9 @@ def run_ours(args, w):
             torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        tot = sum(a.elapsed_time(b) for a, b in ev)
-        t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        acc.update(total_ms=float(t.item()), steps=steps, warmup=warm, clocks=clk.summary(),
+        # job time: the slowest rank's
+        total_ms = pdist.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), device="cuda")
+        acc.update(total_ms=total_ms, steps=steps, warmup=warm, clocks=clk.summary(),
                    stats=ctx.palmad_get_stats(), out={k: v.cpu().numpy() for k, v in out.items()}, first=first)
         return acc
 
@@ -393,10 +392,8 @@ def run_ours(args, w):
         ctx.palmad_find_discords(T_pin.numpy(), minL, maxL, K, forms["mixed_tuned"],
                                  heatmap=w.heatmap, heat_out=heat_host.numpy() if heat_host is not None else None)
         e2e_times.append(time.perf_counter() - t0)
-    e2e_t = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = units * len(e2e_times) * world / float(e2e_t.item()) if e2e_times else None
+    e2e_s = pdist.max_over_ranks(sum(e2e_times), device="cuda")
+    e2e_value = units * len(e2e_times) * world / e2e_s if e2e_times else None
     heat_bytes = 4 * L * (n - minL + 1) if w.heatmap else 0
 
     if rank == 0:

@@ -93,8 +93,8 @@ typedef struct {
     int32_t profile;         /* 1: time every kernel launch with CUDA events
                                 (palmad_get_stats) */
     int32_t pool_slots;      /* cap on the survivors refined at once (0 = as many as
-                                about 1 GiB of per-survivor buffers holds); more
-                                survivors are refined in several rounds */
+                                about 4 GiB of per-survivor buffers holds, at most
+                                131072); more survivors are refined in several rounds */
     int32_t direct_below;    /* 0: the plan's own split between the refine forms; k > 0:
                                 every strip with fewer than k survivors uses the direct
                                 form (k = 129 sends every survivor there) */

@@ -41,7 +41,7 @@ constexpr int kRefineSeg = 1024;      // refine sweep columns per work item (mul
 constexpr int kRefineSegLong = 2048;  // ... and for passes with many columns (lanes x N >= kLongPass)
 constexpr int64_t kLongPass = 2000000;
 constexpr int kMaxLanes = 4096;      // lanes per pass
-constexpr int64_t kPoolBytes = int64_t(1) << 30;  // per-chunk maxima of the refine pool
+constexpr int64_t kPoolBytes = int64_t(1) << 32;  // per-chunk maxima of the refine pool (4 GiB)
 constexpr int64_t kSeedBytes = int64_t(1) << 30;  // tensor-core top-row seeds of the refine sweep
 
 template <class T>
