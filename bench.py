@@ -53,7 +53,7 @@ FIXTURE = os.path.join(ROOT, "tests", "golden", "beats1m_windows.json")
 # k_refine_tcs: beats1m m = 150..157, one launch of 54 684 tiles of 128 x 256
 # survivor-column pairs, 37.6 MB read + 159.4 MB written (the chunk maxima).
 TRAFFIC: dict[str, tuple[str, float]] = {
-    "refine_direct_tc": ("02d557a4a8607e7f", 197.0e6 / (54684 * 128 * 256)),
+    "refine_direct_tc": ("aa47512157115605", 197.0e6 / (54684 * 128 * 256)),
 }
 
 

@@ -29,10 +29,10 @@
 // Seven producer warps keep the ring ahead of the MMAs (with three, the MMA
 // warp waited on them for about a quarter of its time).
 // Ring slots and accumulators are handed over with mbarriers (full / empty
-// per slot, a second release per slot for the column records the epilogue
-// reads, full / empty per accumulator).  The survivor operand is staged by
-// every thread at the start of a work item (128 survivors x up to 8192
-// columns).  Every wait is bounded; a thread whose wait gives up raises a
+// per slot, a second release per slot for the column factors and chunk
+// bounds the epilogue reads, full / empty per accumulator).  The survivor
+// operand is staged by every thread at the start of a work item (128
+// survivors x up to 8192 columns).  Every wait is bounded; a thread whose wait gives up raises a
 // shared abort flag, every role leaves its tile loop, and the CTA reports the
 // error through p.err.
 //
