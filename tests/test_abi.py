@@ -89,6 +89,39 @@ int main(void) {
                    O.autotune.offset, S.tune_ms.offset, S.hint_kills.offset, ctypes.sizeof(R), R.default_ms.offset]
 
 
+def test_every_field_offset_matches_header(tmp_path):
+    """Every field of the ctypes mirrors (palmad_options, palmad_stats,
+    palmad_tune_report) sits at the offset the C compiler gives it."""
+    import subprocess
+    from paper_2304_01660_gb300 import palmad
+    mirrors = {"palmad_options": palmad.Options, "palmad_stats": palmad.Stats,
+               "palmad_tune_report": palmad.TuneReport}
+    lines = []
+    for cname, cls in mirrors.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    probe = tmp_path / "fields.c"
+    probe.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "palmad.h"\nint main(void) {\n'
+                     + "\n".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "fields"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(probe), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line)
+    for cname, cls in mirrors.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(cls, fname).offset, f"{cname}.{fname}"
+
+
+def test_tensor_core_options_default_to_automatic(lib):
+    from paper_2304_01660_gb300 import palmad
+    o = palmad.palmad_default_options()
+    # refine form split for long windows, strip height, MMA survivor group,
+    # column chunks and the tensor-core kernel form all start automatic
+    assert (o.direct_below_long, o.refine_rows, o.tc_group, o.tc_chunks, o.tc_form) == (0, 0, 0, 0, 0)
+
+
 def test_create_without_gpu_fails_cleanly(lib):
     import torch
     if torch.cuda.is_available():
